@@ -1,0 +1,18 @@
+"""Seeded synthetic atmospheres shared by the CPU oracle and the CUDA path.
+
+This package only draws random fields and lays out the model parameters of each
+workload (opacity/source-function stratification, sparsity, line parameters,
+quadrature directions).  It holds none of the formal-solution arithmetic: no
+line-profile evaluation, no ray traversal, no mipmapping.  Both the oracle and
+the CUDA path start from the float32 arrays returned here.
+"""
+
+from .atmospheres import (  # noqa: F401
+    SEED_BASE,
+    lognormal_field,
+    smooth_uniform_field,
+    directions,
+    dense_exponential,
+    sparse_line_atmosphere,
+    gaussian_field,
+)

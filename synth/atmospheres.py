@@ -1,0 +1,166 @@
+"""Seeded synthetic model atmospheres (2D, x horizontal, z vertical, unit cells).
+
+Arrays are indexed ``[z][x]`` (row ``j`` has cell-centre height ``z = j + 0.5``,
+row 0 at the bottom).  Every field is returned as float32: that rounding is the
+input both the oracle (which widens it to float64) and the CUDA path see.
+
+The workloads follow the synthetic stand-ins for the paper's solar models
+(the paper's KHI prominence snapshot and atomic data are not available):
+
+* ``dense_exponential``: an exponentially stratified, lognormally perturbed
+  opacity with a smooth source function and a transparent top 30% of rows,
+  single wavelength.
+* ``sparse_line_atmosphere``: material below a corrugated transition height,
+  zero-opacity corona above it (so whole blocks are empty), a stratified
+  continuum plus one line with Gaussian-shaped opacity whose strength and
+  Doppler width vary smoothly over the model.
+
+Nothing here evaluates the radiative-transfer method itself: line profiles,
+emissivity/opacity sums, traversal and mipmapping live on either side.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import ndtr
+
+SEED_BASE = 2511_08498
+
+
+def _gaussian_filter_fft(white: np.ndarray, corr: float) -> np.ndarray:
+    """Periodic Gaussian smoothing (standard deviation ``corr`` cells) of a white field."""
+    freqs = [np.fft.fftfreq(n) for n in white.shape]
+    k2 = np.zeros(white.shape)
+    for ax, f in enumerate(freqs):
+        shp = [1] * white.ndim
+        shp[ax] = -1
+        k2 = k2 + f.reshape(shp) ** 2
+    transfer = np.exp(-2.0 * np.pi ** 2 * corr ** 2 * k2)
+    g = np.fft.ifftn(np.fft.fftn(white) * transfer).real
+    g = g - g.mean()
+    std = g.std()
+    return g / std if std > 0 else g
+
+
+def gaussian_field(shape, corr: float, rng: np.random.Generator) -> np.ndarray:
+    """Zero-mean, unit-variance, periodic Gaussian random field with correlation length ``corr``."""
+    return _gaussian_filter_fft(rng.standard_normal(shape), corr)
+
+
+def lognormal_field(shape, sigma: float, corr: float, rng: np.random.Generator) -> np.ndarray:
+    """exp(sigma * g) for a unit-variance correlated Gaussian field g (median 1)."""
+    return np.exp(sigma * gaussian_field(shape, corr, rng))
+
+
+def smooth_uniform_field(shape, corr: float, rng: np.random.Generator) -> np.ndarray:
+    """Correlated field with a uniform(0, 1) marginal (normal CDF of a Gaussian field)."""
+    return ndtr(gaussian_field(shape, corr, rng))
+
+
+def directions(n_dir: int, offset: float = 0.5):
+    """Uniform in-plane quadrature: theta_k = 2*pi*(k + offset)/n_dir, weights 1/n_dir.
+
+    Returns ``(dirs, weights)`` with ``dirs[k] = (cos theta_k, sin theta_k)`` as float32
+    (x, z components) and float32 weights.  ``offset=0`` yields axis-parallel rays.
+    """
+    k = np.arange(n_dir, dtype=np.float64)
+    th = 2.0 * np.pi * (k + offset) / n_dir
+    dirs = np.stack([np.cos(th), np.sin(th)], axis=1).astype(np.float32)
+    w = np.full(n_dir, 1.0 / n_dir, dtype=np.float32)
+    return dirs, w
+
+
+def dense_exponential(nx: int = 128, nz: int = 128, seed: int = SEED_BASE + 1,
+                      chi0: float = 1e-3, scale_height: float = 16.0,
+                      sigma: float = 0.5, corr: float = 4.0, top_zero_frac: float = 0.3):
+    """Dense single-wavelength model.
+
+    chi = chi0 * exp(-z/H) * LN(sigma, corr); S = 1 + 0.5 sin(2 pi x / 64) exp(-z/40);
+    eta = chi * S; the top ``floor(top_zero_frac * nz)`` rows have chi = eta = 0.
+    Returns float32 ``eta``, ``chi`` of shape ``[1][nz][nx]`` (wavelength-major).
+    """
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx, dtype=np.float64) + 0.5
+    z = np.arange(nz, dtype=np.float64) + 0.5
+    ln = lognormal_field((nz, nx), sigma, corr, rng)
+    chi = chi0 * np.exp(-z / scale_height)[:, None] * ln
+    src = 1.0 + 0.5 * np.sin(2.0 * np.pi * x / 64.0)[None, :] * np.exp(-z / 40.0)[:, None]
+    n_top = int(np.floor(top_zero_frac * nz))
+    if n_top > 0:
+        chi[nz - n_top:, :] = 0.0
+    chi32 = chi.astype(np.float32)
+    # eta is formed from the rounded chi so that eta == 0 exactly where chi == 0
+    eta32 = (chi32.astype(np.float64) * src).astype(np.float32)
+    return {"eta": eta32[None], "chi": chi32[None], "source": src.astype(np.float32)}
+
+
+def _transition_height(nx: int, nz: int, block: int, empty_frac: float, rng: np.random.Generator):
+    x = np.arange(nx, dtype=np.float64) + 0.5
+    phase = rng.uniform(0.0, 2.0 * np.pi)
+    noise = 5.0 * gaussian_field((nx,), 8.0, rng)
+    amp = nz / 1024.0  # corrugation scales with the model height
+    shape = amp * (40.0 * np.sin(2.0 * np.pi * x / 256.0) + 15.0 * np.sin(2.0 * np.pi * x / 61.0 + phase)) + noise
+    nbx, nbz = nx // block, nz // block
+    col_max = shape.reshape(nbx, block).max(axis=1)
+    bottoms = np.arange(nbz) * block + 0.5  # lowest cell-centre height of each block row
+
+    def frac(z0):
+        return float((bottoms[None, :] >= (z0 + col_max)[:, None]).mean())
+
+    lo, hi = -float(shape.max()) - 1.0, float(nz) + float(-shape.min()) + 1.0
+    for _ in range(80):  # bisection: frac(z0) is non-increasing in z0
+        mid = 0.5 * (lo + hi)
+        if frac(mid) > empty_frac:
+            lo = mid
+        else:
+            hi = mid
+    z0 = lo if abs(frac(lo) - empty_frac) <= abs(frac(hi) - empty_frac) else hi
+    return z0 + shape, frac(z0)
+
+
+def sparse_line_atmosphere(nx: int = 1024, nz: int = 1024, block: int = 16, n_lambda: int = 32,
+                           empty_frac: float = 0.4, seed: int = SEED_BASE + 2,
+                           sigma: float = 0.5, corr: float = 4.0, scale_height: float = 64.0,
+                           ratio_range=(1e2, 1e5), dld_range=(1.0, 3.0)):
+    """Sparse block model with a continuum plus one line (static medium).
+
+    Below the corrugated transition height ``z_tr(x)`` (tuned so that ``empty_frac`` of
+    the ``block``-sized blocks lie wholly above it) the continuum opacity grows downward,
+    ``chi_c = 1e-3 exp(d / H) LN(sigma, corr)`` with depth ``d = z_tr - z``; above it every
+    quantity is zero.  Line parameters per cell: peak line-to-continuum opacity ratio
+    ``ratio`` (log-uniform over ``ratio_range`` as a smooth field) and Doppler width
+    ``dld`` in wavelength-grid units.  ``dlam`` holds the ``n_lambda`` wavelength offsets
+    from line centre, spaced one grid unit apart and centred on the line.
+    Returns float32 fields ``[nz][nx]`` plus ``dlam`` and bookkeeping.
+    """
+    if nx % block or nz % block:
+        raise ValueError("model extent must be a whole number of blocks")
+    rng = np.random.default_rng(seed)
+    z_tr, frac = _transition_height(nx, nz, block, empty_frac, rng)
+    x = np.arange(nx, dtype=np.float64) + 0.5
+    z = np.arange(nz, dtype=np.float64) + 0.5
+    depth = z_tr[None, :] - z[:, None]
+    inside = depth > 0.0
+    ln = lognormal_field((nz, nx), sigma, corr, rng)
+    chi_c = np.where(inside, 1e-3 * np.exp(np.minimum(depth, 60.0 * scale_height) / scale_height) * ln, 0.0)
+    d_pos = np.maximum(depth, 0.0)
+    s_c = np.where(inside, 1.0 + d_pos / 256.0
+                   + 0.5 * np.sin(2.0 * np.pi * x / 64.0)[None, :] * np.exp(-d_pos / 40.0), 0.0)
+    s_l = np.where(inside, s_c * (0.3 + 0.7 * (1.0 - np.exp(-d_pos / 24.0))), 0.0)
+    u1 = smooth_uniform_field((nz, nx), 32.0, rng)
+    u2 = smooth_uniform_field((nz, nx), 32.0, rng)
+    lr0, lr1 = np.log10(ratio_range[0]), np.log10(ratio_range[1])
+    ratio = 10.0 ** (lr0 + (lr1 - lr0) * u1)
+    dld = dld_range[0] + (dld_range[1] - dld_range[0]) * u2
+    dlam = (np.arange(n_lambda, dtype=np.float64) - 0.5 * (n_lambda - 1)).astype(np.float32)
+    return {
+        "chi_c": chi_c.astype(np.float32),
+        "s_c": s_c.astype(np.float32),
+        "s_l": s_l.astype(np.float32),
+        "ratio": ratio.astype(np.float32),
+        "dld": dld.astype(np.float32),
+        "dlam": dlam,
+        "z_tr": z_tr.astype(np.float32),
+        "empty_block_frac": frac,
+        "block": block,
+    }
