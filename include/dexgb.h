@@ -1,0 +1,136 @@
+/*
+ * dexgb -- GB300 (sm_103a) formal solution of the radiative transfer equation
+ * on sparse, variance-limited mipmapped 2D grids (arxiv 2511.08498).
+ *
+ * C ABI.  Every entry point takes plain pointers and sizes; no C++ or PyTorch
+ * types cross this boundary.
+ *
+ * Conventions
+ *  - Geometry: a 2D grid of nx * nz unit square voxels ("cells"), x horizontal,
+ *    z vertical; cell (i, j) has index c = j * nx + i and centre (i + 0.5, j + 0.5).
+ *    Per-cell arrays are row-major [nz][nx]; wavelength-dependent ones are
+ *    wavelength-major [n_lambda][nz][nx] unless stated otherwise.
+ *  - Emissivity eta and opacity chi are per unit length (cell side = 1).
+ *  - Ownership: the caller allocates and owns every buffer passed in; pointers
+ *    marked "device" must be device memory of the context's GPU, "host" must be
+ *    host memory.  The library keeps no pointer after a call returns, except the
+ *    context's own status word.
+ *  - Asynchrony: compute calls enqueue kernels on the context's stream and
+ *    return before they finish.  Argument errors are returned immediately as a
+ *    status code (nothing is enqueued).  Errors found on the device (a ray
+ *    exceeding its step cap, a negative or NaN opacity) are recorded in the
+ *    context's device status word and reported by dex_ctx_check().
+ *  - No call falls back to the CPU: without a usable GPU, dex_ctx_create fails.
+ */
+#ifndef DEXGB_H
+#define DEXGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status -- */
+enum {
+    DEX_OK = 0,
+    DEX_ERR_ARG = 1,            /* invalid argument (nothing was enqueued)           */
+    DEX_ERR_CUDA = 2,           /* a CUDA runtime call failed                         */
+    DEX_ERR_TRAVERSAL_CAP = 4,  /* device: a ray exceeded its traversal step cap      */
+    DEX_ERR_NUMERIC = 8,        /* device: negative or non-finite opacity/emissivity  */
+    DEX_ERR_UNSUPPORTED = 16    /* configuration outside the compiled variants        */
+};
+
+#define DEX_VERSION 100
+#define DEX_MAX_DIRS 256        /* quadrature directions per solve                    */
+#define DEX_BLOCK 16            /* block side of the sparse grid (Section 2.3)        */
+#define DEX_STATE_BITS 3        /* bits per packed block state (Section 2.3.1)        */
+#define DEX_STATES_PER_WORD 21  /* floor(64 / 3) block states per 64-bit word         */
+
+typedef struct dex_ctx dex_ctx;
+
+/* Library version (DEX_VERSION). */
+int dex_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* dex_status_string(int status);
+
+/*
+ * Create a context bound to CUDA device `device` and stream `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  Allocates one 4-byte device
+ * status word.  Returns DEX_ERR_CUDA when no usable device exists.
+ */
+int dex_ctx_create(int device, void* stream, dex_ctx** out);
+
+/* Destroy a context (waits for its stream, frees the status word). NULL is a no-op. */
+int dex_ctx_destroy(dex_ctx* ctx);
+
+/* Rebind the context to another stream of the same device. */
+int dex_ctx_set_stream(dex_ctx* ctx, void* stream);
+
+/*
+ * Synchronise the context's stream, read and clear the device status word.
+ * Returns DEX_OK or the OR of the device error bits (DEX_ERR_TRAVERSAL_CAP,
+ * DEX_ERR_NUMERIC), or DEX_ERR_CUDA if the stream reported a CUDA error.
+ */
+int dex_ctx_check(dex_ctx* ctx);
+
+/* Message of the last error returned by a call on this context (static until the next call). */
+const char* dex_last_error(const dex_ctx* ctx);
+
+/* ------------------------------------------------- wavelength-batch planes --
+ *
+ * The solvers read per-voxel data as interleaved wavelength-batch records: for
+ * a batch width W (1, 2, 4 or 8) and n_batch = ceil(n_lambda / W) batches,
+ *     planes[b][c][0 .. W-1]   = S (source function) of wavelengths b*W + w
+ *     planes[b][c][W .. 2W-1]  = chi of the same wavelengths
+ * with S = eta / chi where chi > 0 and S = eta where chi == 0 (a transparent
+ * emitter; the solvers then add eta * length).  Wavelengths beyond n_lambda
+ * are zero.  One record is 8*W bytes, so a W = 8 record is one 64-byte unit.
+ */
+
+/*
+ * Pack eta, chi ([n_lambda][n_cells] float32, device) into planes
+ * ([n_batch][n_cells][2W] float32, device).  A negative or non-finite chi or
+ * eta sets DEX_ERR_NUMERIC in the device status word (the value is stored as 0).
+ */
+int dex_pack_planes(dex_ctx* ctx, int n_cells, int n_lambda, int W,
+                    const float* eta, const float* chi, float* planes);
+
+/* Number of floats of the planes array: n_batch * n_cells * 2W. */
+size_t dex_planes_floats(int n_cells, int n_lambda, int W);
+
+/* ------------------------------------------------------ plain formal solve --
+ *
+ * Section 1, Eq. RteIntegral with eta, chi constant per voxel (Section 4.1);
+ * long characteristics (Section 1): from the centre of every probe cell, along
+ * each quadrature direction d_k, the ray p(t) = p_c + t d_k is traced to the
+ * grid boundary through the full-resolution grid with exact per-voxel path
+ * lengths (Amanatides & Woo DDA, Section 2.3).  I_k is the intensity arriving
+ * at the probe along that ray from the boundary, where it equals i_bc:
+ *     I_k = i_bc e^{-sum tau} + sum_i S_i (1 - e^{-tau_i}) e^{-sum_{j<i} tau_j},
+ * voxels i ordered from the probe outward, tau_i = chi_i l_i.
+ * J = sum_k w_k I_k (mean intensity).
+ *
+ *   nx, nz     grid size (1 .. 65536 each)
+ *   planes     device, wavelength-batch records of every cell (layout above)
+ *   dirs       host [n_dir][2] (d_x, d_z), unit vectors; weights host [n_dir];
+ *              1 <= n_dir <= DEX_MAX_DIRS
+ *   probes     device [n_probe] cell indices, or NULL: every cell, probe p = c
+ *   J          device [n_lambda][n_probe] float32 output (overwritten)
+ *   I          device [n_lambda][n_dir][n_probe] float32 output, or NULL
+ *   seg_count  device uint64 accumulator, or NULL: adds the number of
+ *              non-zero-length voxel segments traversed (one per ray and voxel,
+ *              counted once per wavelength batch)
+ */
+int dex_formal_solve_dense(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const float* planes,
+                           int n_dir, const float* dirs, const float* weights,
+                           int n_probe, const int* probes, float i_bc,
+                           float* J, float* I, unsigned long long* seg_count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DEXGB_H */

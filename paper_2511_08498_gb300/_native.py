@@ -1,0 +1,62 @@
+"""ctypes loader for libdexgb.so (the C ABI declared in include/dexgb.h).
+
+The library is built in-tree by :mod:`paper_2511_08498_gb300.build`.  There is no
+fallback: if the library cannot be built or loaded, :func:`lib` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+c_int, c_float, c_size_t, c_void_p, c_char_p = ctypes.c_int, ctypes.c_float, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_char_p
+c_u64p = ctypes.POINTER(ctypes.c_ulonglong)
+c_fp = ctypes.POINTER(ctypes.c_float)
+
+# name -> (restype, argtypes); device pointers are passed as c_void_p
+PROTOTYPES = {
+    "dex_version": (c_int, []),
+    "dex_status_string": (c_char_p, [c_int]),
+    "dex_ctx_create": (c_int, [c_int, c_void_p, ctypes.POINTER(c_void_p)]),
+    "dex_ctx_destroy": (c_int, [c_void_p]),
+    "dex_ctx_set_stream": (c_int, [c_void_p, c_void_p]),
+    "dex_ctx_check": (c_int, [c_void_p]),
+    "dex_last_error": (c_char_p, [c_void_p]),
+    "dex_planes_floats": (c_size_t, [c_int, c_int, c_int]),
+    "dex_pack_planes": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "dex_formal_solve_dense": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_int, c_fp, c_fp,
+                                       c_int, c_void_p, c_float, c_void_p, c_void_p, c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) libdexgb.so and declare its prototypes."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"libdexgb.so missing at {path}")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in PROTOTYPES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+class DexError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dexgb error {code}: {msg}")
+        self.code = code

@@ -1,0 +1,178 @@
+// Plain full-resolution formal solver (long characteristics + Amanatides & Woo DDA)
+// and the packing of eta/chi into interleaved wavelength-batch records.
+//
+// Thread = (probe, wavelength batch).  Each thread walks every quadrature
+// direction in turn, so the angular sum J = sum_k w_k I_k stays in registers
+// and needs no atomics.  Lanes of a warp hold neighbouring probes and share the
+// direction, so their voxels are neighbours in memory and their step counts
+// match.  Wavelength batch is the slowest grid dimension so that one batch
+// (nx * nz * 8W bytes) is the L2-resident working set at a time.
+//
+// Plane crossings are evaluated from the integer voxel offset,
+//   t_next = (offset + 1/2) / d,
+// instead of being accumulated (t += 1/d): every t is then within one rounding
+// of exact, and the boundary plane's t is bit-identical to the exit parameter,
+// so a ray can never step outside the grid.
+#include "dex_internal.h"
+
+#include <cfloat>
+
+namespace dex {
+
+namespace {
+
+__global__ void k_pack_planes(long long n_cells, int n_lambda, int W, int n_batch,
+                              const float* __restrict__ eta, const float* __restrict__ chi,
+                              float* __restrict__ planes, unsigned int* status)
+{
+    const long long total = n_cells * n_batch;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const long long c = q % n_cells;
+        const int b = (int)(q / n_cells);
+        float* rec = planes + q * (2 * W);
+        bool bad = false;
+        for (int w = 0; w < W; ++w) {
+            const int l = b * W + w;
+            float S = 0.0f, x = 0.0f;
+            if (l < n_lambda) {
+                const float e = eta[(long long)l * n_cells + c];
+                x = chi[(long long)l * n_cells + c];
+                if (!(x >= 0.0f) || !(e >= 0.0f) || !isfinite(x) || !isfinite(e)) {
+                    bad = true;
+                    x = 0.0f;
+                    S = 0.0f;
+                } else {
+                    S = (x > 0.0f) ? e / x : e;
+                }
+            }
+            rec[w] = S;
+            rec[W + w] = x;
+        }
+        if (bad) raise_status(status, DEX_ERR_NUMERIC);
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
+{
+    const float kInf = __int_as_float(0x7f800000);
+    const int b = blockIdx.y;
+    int i, j, p;
+    if (P.probes == nullptr) {
+        // 32 x 8 tile of probes per CTA: lanes along x, warps along z
+        const int tiles_x = (P.nx + 31) >> 5;
+        const int tx = blockIdx.x % tiles_x, tz = blockIdx.x / tiles_x;
+        i = tx * 32 + (threadIdx.x & 31);
+        j = tz * 8 + (threadIdx.x >> 5);
+        if (i >= P.nx || j >= P.nz) return;
+        p = j * P.nx + i;
+    } else {
+        p = blockIdx.x * blockDim.x + threadIdx.x;
+        if (p >= P.n_probe) return;
+        const int c = P.probes[p];
+        if (c < 0 || (long long)c >= P.n_cells) {
+            raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
+            return;
+        }
+        i = c % P.nx;
+        j = c / P.nx;
+    }
+
+    const float* __restrict__ base = P.planes + (size_t)b * P.n_cells * (2 * W);
+    const int cap = P.nx + P.nz + 4;
+    float Jw[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) Jw[w] = 0.0f;
+    unsigned int nseg = 0;
+    bool capped = false;
+
+    for (int k = 0; k < P.quad.n_dir; ++k) {
+        const float dx = P.quad.dx[k], dz = P.quad.dz[k];
+        const int sx = dx > 0.0f ? 1 : -1, sz = dz > 0.0f ? 1 : -1;
+        const float hx = dx < 0.0f ? -0.5f : 0.5f, hz = dz < 0.0f ? -0.5f : 0.5f;
+        const float idx = dx != 0.0f ? 1.0f / dx : kInf;
+        const float idz = dz != 0.0f ? 1.0f / dz : kInf;
+        const float t2x = dx != 0.0f ? ((float)(dx > 0.0f ? P.nx - 1 - i : -i) + hx) * idx : kInf;
+        const float t2z = dz != 0.0f ? ((float)(dz > 0.0f ? P.nz - 1 - j : -j) + hz) * idz : kInf;
+        const float t2 = fminf(t2x, t2z);
+
+        int di = 0, dj = 0;
+        float t = 0.0f;
+        float I[W], T[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
+
+        for (int it = 0;; ++it) {
+            const float tnx = ((float)di + hx) * idx;
+            const float tnz = ((float)dj + hz) * idz;
+            const float th = fminf(fminf(tnx, tnz), t2);
+            const float len = th - t;
+            const int ci = i + di, cj = j + dj;
+            if (it >= cap || (unsigned)ci >= (unsigned)P.nx || (unsigned)cj >= (unsigned)P.nz) {
+                capped = true;
+                break;
+            }
+            const Record<W> r = load_record<W>(base + ((size_t)cj * P.nx + ci) * (2 * W));
+            const float nl2 = len * kNegLog2e;
+#pragma unroll
+            for (int w = 0; w < W; ++w) segment(r.S[w], r.chi[w], nl2, len, I[w], T[w]);
+            nseg += (len > 0.0f);
+            t = th;
+            if (th >= t2) break;
+            if (tnx <= tnz) di += sx; else dj += sz;
+        }
+        const float wk = P.quad.w[k];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const float Iw = fmaf(T[w], P.i_bc, I[w]);
+            Jw[w] = fmaf(wk, Iw, Jw[w]);
+            const int l = b * W + w;
+            if (P.I != nullptr && l < P.n_lambda)
+                P.I[((size_t)l * P.quad.n_dir + k) * P.n_probe + p] = Iw;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+        const int l = b * W + w;
+        if (l < P.n_lambda) P.J[(size_t)l * P.n_probe + p] = Jw[w];
+    }
+    if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
+    if (P.seg_count != nullptr) atomicAdd(P.seg_count, (unsigned long long)nseg);
+}
+
+}  // namespace
+
+cudaError_t launch_pack_planes(cudaStream_t s, long long n_cells, int n_lambda, int W,
+                               const float* eta, const float* chi, float* planes, unsigned int* status)
+{
+    const int n_batch = (n_lambda + W - 1) / W;
+    const long long total = n_cells * n_batch;
+    if (total == 0) return cudaSuccess;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152LL * 64) blocks = 152LL * 64;
+    k_pack_planes<<<(unsigned)blocks, 256, 0, s>>>(n_cells, n_lambda, W, n_batch, eta, chi, planes, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_dense(cudaStream_t s, const DenseParams& P)
+{
+    if (P.n_probe == 0 || P.n_batch == 0) return cudaSuccess;
+    dim3 grid;
+    if (P.probes == nullptr) {
+        const unsigned tiles = (unsigned)(((P.nx + 31) / 32) * ((P.nz + 7) / 8));
+        grid = dim3(tiles, (unsigned)P.n_batch);
+    } else {
+        grid = dim3((unsigned)((P.n_probe + 255) / 256), (unsigned)P.n_batch);
+    }
+    switch (P.W) {
+        case 1: k_solve_dense<1><<<grid, 256, 0, s>>>(P); break;
+        case 2: k_solve_dense<2><<<grid, 256, 0, s>>>(P); break;
+        case 4: k_solve_dense<4><<<grid, 256, 0, s>>>(P); break;
+        case 8: k_solve_dense<8><<<grid, 256, 0, s>>>(P); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dex

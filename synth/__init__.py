@@ -15,4 +15,5 @@ from .atmospheres import (  # noqa: F401
     dense_exponential,
     sparse_line_atmosphere,
     gaussian_field,
+    random_medium,
 )

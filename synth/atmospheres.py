@@ -164,3 +164,33 @@ def sparse_line_atmosphere(nx: int = 1024, nz: int = 1024, block: int = 16, n_la
         "empty_block_frac": frac,
         "block": block,
     }
+
+
+def random_medium(nx: int, nz: int, n_lambda: int, seed: int = SEED_BASE + 100,
+                  log_chi_range=(-4.0, 1.5), corr: float = 3.0,
+                  zero_frac: float = 0.1, emitter_frac: float = 0.02):
+    """Multi-wavelength test medium with structure at every scale the solvers meet.
+
+    Per wavelength, log10 chi is a correlated field spread over ``log_chi_range``
+    (optical depths per cell from ~1e-4 to ~30); S is lognormal around 1.  A
+    ``zero_frac`` share of cells is empty (eta = chi = 0) and an ``emitter_frac``
+    share is a transparent emitter (chi = 0, eta > 0).  Returns float32
+    ``eta``, ``chi`` of shape ``[n_lambda][nz][nx]``.
+    """
+    rng = np.random.default_rng(seed)
+    lo, hi = log_chi_range
+    eta = np.empty((n_lambda, nz, nx), dtype=np.float32)
+    chi = np.empty((n_lambda, nz, nx), dtype=np.float32)
+    zero = rng.random((nz, nx)) < zero_frac
+    emit = (~zero) & (rng.random((nz, nx)) < emitter_frac)
+    for l in range(n_lambda):
+        u = smooth_uniform_field((nz, nx), corr, rng)
+        c = 10.0 ** (lo + (hi - lo) * u)
+        s = lognormal_field((nz, nx), 0.5, corr, rng)
+        c = np.where(zero | emit, 0.0, c).astype(np.float32)
+        e = (c.astype(np.float64) * s)
+        e = np.where(emit, 0.05 * s, e)
+        e = np.where(zero, 0.0, e)
+        chi[l] = c
+        eta[l] = e.astype(np.float32)
+    return {"eta": eta, "chi": chi}

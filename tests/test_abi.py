@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads and exports every entry point declared in include/*.h
+(no compute calls: this runs without a GPU)."""
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2511_08498_gb300 import _native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(dex_\w+)\s*\(", src, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    assert "dex_formal_solve_dense" in names and "dex_ctx_create" in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = _native.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_prototypes_cover_header():
+    assert set(declared_functions()) <= set(_native.PROTOTYPES)
+
+
+def test_version_and_status_strings():
+    L = _native.lib()
+    assert L.dex_version() == 100
+    assert L.dex_status_string(0) == b"ok"
+    assert L.dex_status_string(1) == b"invalid argument"
+
+
+def test_planes_size_arithmetic():
+    L = _native.lib()
+    assert L.dex_planes_floats(10, 11, 4) == 3 * 10 * 8
+    assert L.dex_planes_floats(10, 0, 8) == 0
+    assert L.dex_planes_floats(10, 3, 3) == 0  # unsupported batch width
+
+
+def test_context_creation_fails_cleanly_without_gpu():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert _native.lib().dex_ctx_create(0, None, ctypes.byref(h)) == 2  # DEX_ERR_CUDA
+    assert not h.value

@@ -1,0 +1,130 @@
+"""Plain full-resolution CUDA solve vs the float64 oracle, element by element.
+
+Tolerance: the GPU path computes in float32 and must match the oracle within
+1e-5 relative per intensity; an exact zero must be reproduced exactly.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import lc
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-5
+
+
+def assert_rel(gpu, ref, rtol=RTOL, what=""):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert gpu.shape == ref.shape
+    zero = ref == 0
+    assert np.array_equal(gpu[zero], ref[zero]), f"{what}: exact zeros differ"
+    rel = np.abs(gpu - ref) / np.maximum(np.abs(ref), 1e-30)
+    worst = np.unravel_index(np.argmax(rel), rel.shape)
+    assert rel.max() <= rtol, f"{what}: max rel err {rel.max():.3e} at {worst}: gpu {gpu[worst]} ref {ref[worst]}"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2511_08498_gb300 import api
+    return api.Context(0)
+
+
+def run_dense(ctx, eta, chi, dirs, w, W, probes=None, i_bc=0.0, want_I=True, count=False):
+    from paper_2511_08498_gb300 import api
+    L, nz, nx = eta.shape
+    e = torch.from_numpy(eta.reshape(L, -1)).cuda()
+    c = torch.from_numpy(chi.reshape(L, -1)).cuda()
+    planes = api.pack_planes(ctx, e, c, W)
+    pr = None if probes is None else torch.from_numpy(np.asarray(probes, np.int32)).cuda()
+    J, I, seg = api.formal_solve_dense(ctx, nx, nz, L, W, planes, dirs, w, probes=pr, i_bc=i_bc,
+                                       want_intensity=want_I, count_segments=count)
+    ctx.check()
+    return (J.cpu().numpy(), None if I is None else I.cpu().numpy(),
+            None if seg is None else int(seg.cpu().item()))
+
+
+def test_dense_exponential_full_size(ctx):
+    """The 128^2, 16-direction, single-wavelength exponential atmosphere."""
+    m = synth.dense_exponential()
+    dirs, w = synth.directions(16)
+    Jg, Ig, seg = run_dense(ctx, m["eta"], m["chi"], dirs, w, W=1, count=True)
+    Jr, Ir = lc.formal_solve(m["eta"], m["chi"], dirs, w, want_intensity=True)
+    assert_rel(Ig, Ir, what="I")
+    assert_rel(Jg, Jr, what="J")
+    assert seg == lc.count_segments(128, 128, dirs, np.arange(128 * 128, dtype=np.int32))
+
+
+@pytest.mark.parametrize("W", [1, 2, 4, 8])
+def test_random_medium_ragged(ctx, W):
+    """Ragged tiles (67 x 45), a ragged last wavelength batch (11 wavelengths),
+    optical depths 1e-4..30 per cell, empty cells and transparent emitters, i_bc != 0."""
+    m = synth.random_medium(67, 45, 11, seed=synth.SEED_BASE + 200 + W)
+    dirs, w = synth.directions(12)
+    Jg, Ig, _ = run_dense(ctx, m["eta"], m["chi"], dirs, w, W=W, i_bc=0.3)
+    Jr, Ir = lc.formal_solve(m["eta"], m["chi"], dirs, w, i_bc=0.3, want_intensity=True)
+    assert_rel(Ig, Ir, what=f"I W={W}")
+    assert_rel(Jg, Jr, what=f"J W={W}")
+
+
+def test_axis_parallel_and_corner_rays(ctx):
+    """theta_k = 2 pi k / 8: axis-parallel rays and diagonals through voxel corners."""
+    m = synth.random_medium(40, 33, 8, seed=synth.SEED_BASE + 300)
+    dirs, w = synth.directions(8, offset=0.0)
+    Jg, Ig, seg = run_dense(ctx, m["eta"], m["chi"], dirs, w, W=8, count=True)
+    Jr, Ir = lc.formal_solve(m["eta"], m["chi"], dirs, w, want_intensity=True)
+    assert_rel(Ig, Ir, what="I")
+    assert seg == lc.count_segments(40, 33, dirs, np.arange(40 * 33, dtype=np.int32))
+
+
+def test_probe_subset_and_degenerate_sizes(ctx):
+    m = synth.random_medium(50, 37, 5, seed=synth.SEED_BASE + 301)
+    dirs, w = synth.directions(24)
+    rng = np.random.default_rng(5)
+    probes = rng.choice(50 * 37, size=301, replace=False).astype(np.int32)
+    Jg, Ig, _ = run_dense(ctx, m["eta"], m["chi"], dirs, w, W=4, probes=probes)
+    Jr, Ir = lc.formal_solve(m["eta"], m["chi"], dirs, w, probes=probes, want_intensity=True)
+    assert_rel(Ig, Ir, what="I subset")
+    # one-cell grid, one-row grid
+    for nx, nz in [(1, 1), (19, 1), (1, 23)]:
+        mm = synth.random_medium(nx, nz, 3, seed=synth.SEED_BASE + 302 + nx)
+        Jg, Ig, _ = run_dense(ctx, mm["eta"], mm["chi"], dirs, w, W=2)
+        Jr, Ir = lc.formal_solve(mm["eta"], mm["chi"], dirs, w, want_intensity=True)
+        assert_rel(Ig, Ir, what=f"I {nx}x{nz}")
+
+
+def test_empty_probe_list_is_a_no_op(ctx):
+    from paper_2511_08498_gb300 import api
+    m = synth.random_medium(8, 8, 2)
+    dirs, w = synth.directions(4)
+    e = torch.from_numpy(m["eta"].reshape(2, -1)).cuda()
+    planes = api.pack_planes(ctx, e, torch.from_numpy(m["chi"].reshape(2, -1)).cuda(), 2)
+    J = torch.full((2, 0), 7.0, device="cuda")
+    api.formal_solve_dense(ctx, 8, 8, 2, 2, planes, dirs, w, probes=torch.zeros(0, dtype=torch.int32, device="cuda"), J=J)
+    ctx.check()
+
+
+def test_negative_opacity_is_reported(ctx):
+    from paper_2511_08498_gb300 import api
+    from paper_2511_08498_gb300._native import DexError
+    chi = torch.ones((1, 16), device="cuda")
+    chi[0, 3] = -1.0
+    api.pack_planes(ctx, torch.ones((1, 16), device="cuda"), chi, 1)
+    with pytest.raises(DexError) as ei:
+        ctx.check()
+    assert ei.value.code & 8
+    ctx.check()  # the status word was cleared
+
+
+def test_argument_errors_enqueue_nothing(ctx):
+    from paper_2511_08498_gb300 import api
+    from paper_2511_08498_gb300._native import DexError
+    planes = torch.zeros(64, device="cuda")
+    with pytest.raises(DexError):
+        api.formal_solve_dense(ctx, 4, 4, 1, 3, planes, [[1, 0]], [1.0])  # W = 3
+    with pytest.raises(DexError):
+        api.formal_solve_dense(ctx, 4, 4, 1, 1, planes, [[1, 1]], [1.0])  # not a unit vector
+    ctx.check()
