@@ -1,0 +1,417 @@
+"""Benchmark: accelerated (sparse + VLM + HDDA) formal solution on one GB300.
+
+Workload: the 1024 x 1024 sparse static-line atmosphere (16^2 blocks, 40% empty),
+32 wavelengths, 64 directions, VLM levels 0-3 with IoD thresholds 1e-2 (timed
+step) and 1e-3 (reported beside it), FP32 -- with the plain full-resolution GPU
+solve of the same probes timed beside it.
+
+One step = the whole accelerated path on device-resident model parameters:
+MIP-0 eta/chi synthesis -> block sparsity map + Morton layout -> MIP chains +
+VLM levels -> HDDA formal solve -> J.  Throughput is counted in dense
+(full-resolution) ray-wavelength voxel segments, so accelerated and plain
+numbers compare as wall-time ratios.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ray-wavelength segments/s and HBM GB/s on 1 GB300; accel vs plain at ≤0.5% p99.9 pop error"
+NX = NZ = 1024
+N_LAMBDA = 32
+N_DIR = 64
+W = 8
+MAX_MIP = 3
+THR = 1e-2
+THR_STRICT = 1e-3
+CHI_DS_MIN = 0.25
+WORKLOAD = (f"sparse static-line atmosphere {NX}x{NZ}, 16^2 blocks, 40% empty, {N_LAMBDA} wavelengths, "
+            f"{N_DIR} directions, VLM mip 0-{MAX_MIP}, IoD threshold {THR:g} (and {THR_STRICT:g}), HDDA, FP32")
+# SM count x SFU ex2 results per clock per SM x max SM clock: each segment-wavelength
+# update needs one exponential, so this bounds the updates per second
+SFU_PER_SM_CLK = 16
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ native --
+
+class Workload:
+    def __init__(self, ctx, seed_offset: int = 0):
+        import torch
+
+        import synth
+        from paper_2511_08498_gb300 import api
+        self.api, self.torch, self.ctx = api, torch, ctx
+        m = synth.sparse_line_atmosphere(NX, NZ, n_lambda=N_LAMBDA, seed=synth.SEED_BASE + 2 + seed_offset)
+        self.host = {k: np.ascontiguousarray(m[k]).reshape(-1) for k in ("chi_c", "s_c", "s_l", "ratio", "dld", "dlam")}
+        self.pinned = {k: torch.from_numpy(v).pin_memory() for k, v in self.host.items()}
+        self.dev = {k: v.cuda() for k, v in self.pinned.items()}
+        self.dirs, self.w = synth.directions(N_DIR)
+        n_cells = NX * NZ
+        self.eta = torch.empty((N_LAMBDA, n_cells), dtype=torch.float32, device="cuda")
+        self.chi = torch.empty_like(self.eta)
+        self.J = torch.empty_like(self.eta)
+        self.grid = None
+        self.mips = None
+        self.launches_per_step = 5  # synth, block flags, block layout, mips build, hdda solve
+
+    def synth(self):
+        d = self.dev
+        self.api.synth_static_line(self.ctx, d["chi_c"], d["s_c"], d["s_l"], d["ratio"], d["dld"], d["dlam"],
+                                   eta=self.eta, chi=self.chi)
+
+    def step(self, thr=THR, ev=None, count=False):
+        api = self.api
+        self.synth()
+        self.grid = api.grid_build(self.ctx, NX, NZ, self.eta, self.chi, out=self.grid)
+        self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, W, MAX_MIP, thr, thr, CHI_DS_MIN,
+                                   out=self.mips)
+        if ev is not None:
+            ev[0].record()
+        _, _, seg = api.formal_solve_hdda(self.ctx, self.grid, self.mips, self.dirs, self.w, J=self.J,
+                                          count_segments=count)
+        if ev is not None:
+            ev[1].record()
+        return seg
+
+    def probes(self):
+        grid = self.grid
+        off = grid.block_offset.view(grid.nbz, grid.nbx) >= 0
+        cell = off.repeat_interleave(16, 0).repeat_interleave(16, 1).reshape(-1)
+        return self.torch.nonzero(cell).to(self.torch.int32).reshape(-1)
+
+
+def l2_flush(buf):
+    buf.add_(1.0)  # writes 256 MiB > 129 MB L2
+
+
+def time_steps(fn, steps, warmup, torch, flush):
+    for _ in range(warmup):
+        fn(None)
+    torch.cuda.synchronize()
+    times, inner = [], []
+    for _ in range(steps):
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn((k0, k1))
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        inner.append(k0.elapsed_time(k1))
+    return times, inner
+
+
+def native(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2511_08498_gb300 import api
+    ctx = api.Context(local)
+    wl = Workload(ctx, seed_offset=rank)
+    flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def flush():
+        l2_flush(flush_buf)
+
+    # --- untimed: dense-equivalent segment count, plain reference J, executed segment counts
+    seg_acc = wl.step(count=True)
+    probes = wl.probes()
+    n_probe = int(probes.numel())
+    J_acc = wl.J.clone()
+    planes = api.pack_planes(ctx, wl.eta, wl.chi, W)
+    Jp, _, seg_dense = api.formal_solve_dense(ctx, NX, NZ, N_LAMBDA, W, planes, wl.dirs, wl.w, probes=probes,
+                                              count_segments=True)
+    seg_strict = wl.step(thr=THR_STRICT, count=True)
+    J_strict = wl.J.clone()
+    ctx.check()
+    n_batch = -(-N_LAMBDA // W)
+    dense_seg_lambda = int(seg_dense.item()) * W          # counted once per batch of W wavelengths
+    exec_seg_lambda = int(seg_acc.item()) * W
+    exec_seg_lambda_strict = int(seg_strict.item()) * W
+    Jp_probe = Jp.double()
+    acc_probe = J_acc[:, probes.long()].double()
+    strict_probe = J_strict[:, probes.long()].double()
+
+    def err_pct(a):
+        rel = ((a - Jp_probe).abs() / Jp_probe.abs().clamp_min(1e-30)).flatten().cpu().numpy() * 100.0
+        return {q: float(np.percentile(rel, p)) for q, p in
+                (("p50", 50), ("p99", 99), ("p99.9", 99.9), ("max", 100))}
+
+    levels = api.unpack_states(wl.mips.words.cpu().numpy(), wl.grid.n_blocks)
+    level_frac = [float((levels == m).sum()) / float((levels >= 0).sum()) for m in range(MAX_MIP + 1)]
+
+    # --- timed: accelerated steps
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        times, hdda_times = time_steps(lambda ev: wl.step(ev=ev), args.steps, args.warmup, torch, flush)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_s = sum(times) / 1e3
+    if world > 1:
+        t = torch.tensor([step_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_s = float(t.item())
+    total_units = dense_seg_lambda * args.steps * world
+    value = total_units / step_s
+    ms_per_step = step_s * 1e3 / args.steps
+    hdda_s = sum(hdda_times) / 1e3 / args.steps
+
+    # --- plain full-resolution path, same probes and timing protocol
+    def plain_step(ev):
+        wl.synth()
+        api.pack_planes(ctx, wl.eta, wl.chi, W, out=planes)
+        if ev is not None:
+            ev[0].record()
+        api.formal_solve_dense(ctx, NX, NZ, N_LAMBDA, W, planes, wl.dirs, wl.w, probes=probes, J=Jp)
+        if ev is not None:
+            ev[1].record()
+    p_steps = max(2, min(args.steps, 3))
+    ptimes, pkern = time_steps(plain_step, p_steps, 1, torch, flush)
+    plain_s = sum(ptimes) / 1e3 / p_steps
+    plain_kern_s = sum(pkern) / 1e3 / p_steps
+
+    # strict threshold, same protocol
+    stimes, skern = time_steps(lambda ev: wl.step(thr=THR_STRICT, ev=ev), max(2, min(args.steps, 3)), 1, torch, flush)
+    strict_s = sum(stimes) / 1e3 / len(stimes)
+
+    # --- end to end through the API with host buffers (H2D params, D2H J)
+    J_host = torch.empty((N_LAMBDA, NX * NZ), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in wl.pinned.values())
+    d2h = J_host.numel() * J_host.element_size()
+
+    def e2e_step(ev):
+        for k, v in wl.pinned.items():
+            wl.dev[k].copy_(v, non_blocking=True)
+        wl.step()
+        J_host.copy_(wl.J, non_blocking=True)
+    etimes, _ = time_steps(lambda ev: (e2e_step(ev), ev[0].record() if ev else None, ev[1].record() if ev else None),
+                           args.steps, 1, torch, flush)
+    e2e_s = sum(etimes) / 1e3
+    ctx.check()
+
+    peaks, peak_src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sfu_peak = N_SM * SFU_PER_SM_CLK * sm_max * 1e6 / 1e9  # G updates / s
+    achieved = exec_seg_lambda / hdda_s / 1e9
+    plain_achieved = dense_seg_lambda / plain_kern_s / 1e9
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "seg-lambda/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "probes": n_probe, "dense_seg_lambda_per_step": dense_seg_lambda,
+                   "l2": "flushed between steps (256 MiB write); inputs and bricks also exceed L2",
+                   "timing": "CUDA events per step on the launch stream, flush outside the events",
+                   "parallelism": "one independent atmosphere per rank (weak scaling, no collective)"},
+        "roofline": {"bound": "alu", "kernel": "k_solve_hdda<8>", "achieved": achieved, "peak": sfu_peak,
+                     "unit": "G seg-lambda updates/s", "frac": achieved / sfu_peak, "traffic": None,
+                     "peak_basis": f"{N_SM} SMs x {SFU_PER_SM_CLK} ex2/clk x {sm_max:.0f} MHz (one exponential "
+                                   "per segment-wavelength update)",
+                     "kernel_ms": hdda_s * 1e3, "executed_seg_lambda": exec_seg_lambda,
+                     "hbm_algorithmic_gbs": exec_seg_lambda * 8 / hdda_s / 1e9,
+                     "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "peak_source": peak_src},
+        "plain": {"value": dense_seg_lambda / plain_s, "ms_per_step": plain_s * 1e3,
+                  "kernel_ms": plain_kern_s * 1e3, "kernel_updates_per_s": plain_achieved * 1e9,
+                  "kernel_frac_of_sfu_peak": plain_achieved / sfu_peak,
+                  "hbm_algorithmic_gbs": dense_seg_lambda * 8 / plain_kern_s / 1e9},
+        "speedup_vs_plain": plain_s / (ms_per_step / 1e3),
+        "j_err_pct_vs_plain": err_pct(acc_probe),
+        "strict": {"iod_threshold": THR_STRICT, "ms_per_step": strict_s * 1e3,
+                   "value": dense_seg_lambda / strict_s, "speedup_vs_plain": plain_s / strict_s,
+                   "executed_seg_lambda": exec_seg_lambda_strict, "j_err_pct_vs_plain": err_pct(strict_probe)},
+        "mip_level_fraction": level_frac,
+        "e2e": {"value": dense_seg_lambda * args.steps / e2e_s, "unit": "seg-lambda/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": wl.launches_per_step * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, probes.cpu().numpy())
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# --------------------------------------------------------- oracle on CPU --
+
+def cpu_sample(m, n_probe_sample, seed=0):
+    """The oracle's formal solve over a seeded sample of the workload's probes.
+
+    Returns (dense seg-lambda of the sample, seconds, threads, description)."""
+    from oracle import lc, lines, mips
+    import synth
+    eta, chi = lines.line_eta_chi(m["chi_c"], m["s_c"], m["s_l"], m["ratio"], m["dld"], m["dlam"])
+    empty = mips.block_empty(eta, chi, 16)
+    probes = mips.probes_of_blocks(empty, 16)
+    rng = np.random.default_rng(seed)
+    sample = np.sort(rng.choice(probes, size=min(n_probe_sample, probes.size), replace=False)).astype(np.int32)
+    dirs, w = synth.directions(N_DIR)
+    segs = lc.count_segments(NX, NZ, dirs, sample)
+    t0 = time.perf_counter()
+    lc.formal_solve(eta, chi, dirs, w, probes=sample)
+    dt = time.perf_counter() - t0
+    desc = (f"{sample.size} of {probes.size} probes (seeded), all {N_DIR} directions x {N_LAMBDA} wavelengths, "
+            "float64 plain long characteristics on the MIP-0 grid (the oracle has no acceleration); "
+            "eta/chi synthesis excluded")
+    return segs * N_LAMBDA, dt, lc.num_threads(), desc
+
+
+def cpu_baseline(wl, probes_np):
+    import synth
+    m = synth.sparse_line_atmosphere(NX, NZ, n_lambda=N_LAMBDA, seed=synth.SEED_BASE + 2)
+    units, dt, threads, desc = cpu_sample(m, 2048)
+    return {"value": units / dt, "unit": "seg-lambda/s", "cores": threads, "kind": "oracle", "sample": desc,
+            "seconds": dt}
+
+
+def reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import synth
+    m = synth.sparse_line_atmosphere(NX, NZ, n_lambda=N_LAMBDA, seed=synth.SEED_BASE + 2)
+    for _ in range(args.warmup):
+        cpu_sample(m, 64, seed=1)
+    units = 0
+    secs = 0.0
+    threads, desc = 1, ""
+    for k in range(args.steps):
+        u, dt, threads, desc = cpu_sample(m, 512, seed=100 + k)
+        units += u
+        secs += dt
+    value = units / secs
+    out = {
+        "metric": METRIC, "value": value, "unit": "seg-lambda/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "sample_per_step": desc},
+        "cpu_baseline": {"value": value, "unit": "seg-lambda/s", "cores": threads, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "seg-lambda/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference(args)
+    else:
+        native(args)
+
+
+if __name__ == "__main__":
+    main()

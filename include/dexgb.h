@@ -117,7 +117,9 @@ size_t dex_planes_floats(int n_cells, int n_lambda, int W);
  *   planes     device, wavelength-batch records of every cell (layout above)
  *   dirs       host [n_dir][2] (d_x, d_z), unit vectors; weights host [n_dir];
  *              1 <= n_dir <= DEX_MAX_DIRS
- *   probes     device [n_probe] cell indices, or NULL: every cell, probe p = c
+ *   n_probe    number of probes; n_probe < 0 means every cell (probes must be
+ *              NULL, probe p = cell p); n_probe == 0 is a no-op
+ *   probes     device [n_probe] cell indices (ignored when n_probe <= 0)
  *   J          device [n_lambda][n_probe] float32 output (overwritten)
  *   I          device [n_lambda][n_dir][n_probe] float32 output, or NULL
  *   seg_count  device uint64 accumulator, or NULL: adds the number of
@@ -128,6 +130,93 @@ int dex_formal_solve_dense(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, co
                            int n_dir, const float* dirs, const float* weights,
                            int n_probe, const int* probes, float i_bc,
                            float* J, float* I, unsigned long long* seg_count);
+
+/* ------------------------------------------ static continuum + line model --
+ *
+ * Section 2, Eqs. EtaTot and ChiTot (eta = sum of line terms + background,
+ * chi likewise) for one line over a continuum, with a line profile normalised
+ * to its peak:  chi_l = ratio chi_c exp(-(dlam / dld)^2),  chi = chi_c + chi_l,
+ * eta = chi_c S_c + chi_l S_l.
+ *   chi_c, s_c, s_l, ratio, dld : device [n_cells] (continuum opacity, continuum
+ *                                 and line source functions, peak line/continuum
+ *                                 opacity ratio, Doppler width in the units of dlam)
+ *   dlam                        : device [n_lambda] offsets from line centre
+ *   eta, chi                    : device [n_lambda][n_cells] outputs
+ */
+int dex_synth_static_line(dex_ctx* ctx, int n_cells, int n_lambda, const float* chi_c, const float* s_c,
+                          const float* s_l, const float* ratio, const float* dld, const float* dlam,
+                          float* eta, float* chi);
+
+/* ------------------------------------------------------ sparse block grid --
+ *
+ * Section 2.3: the grid is cut into DEX_BLOCK x DEX_BLOCK blocks (nx and nz must
+ * be multiples of DEX_BLOCK); a block is empty when eta = chi = 0 in all its
+ * cells at every wavelength (one sparsity map shared by all wavelengths,
+ * Section 4.1).  Section 2.3.1: non-empty ("active") blocks are ranked along
+ * the Morton Z-order curve of their block coordinates (bx in the even bits),
+ * and a dense lookup table gives each block's rank.
+ *
+ *   eta, chi      device [n_lambda][nz][nx]
+ *   block_offset  device [nbz * nbx] output: rank of block bz*nbx+bx, or -1 if empty
+ *   active        device [nbz * nbx] output: active[r] = block index of rank r
+ *                 (entries >= *n_active are left untouched)
+ *   n_active      device int output: number of active blocks
+ */
+int dex_grid_build(dex_ctx* ctx, int nx, int nz, int n_lambda, const float* eta, const float* chi,
+                   int* block_offset, int* active, int* n_active);
+
+/* Packed 3-bit block-state words per wavelength batch: ceil(nbx * nbz / 21). */
+size_t dex_state_words(int nx, int nz);
+
+/* Voxel records of one active block's MIP chain, levels 0..max_mip: sum (16 >> m)^2. */
+int dex_chain_voxels(int max_mip);
+
+/* Floats of the brick array: n_batch * capacity * dex_chain_voxels(max_mip) * 2W. */
+size_t dex_brick_floats(int capacity, int n_lambda, int W, int max_mip);
+
+/* Variance-limited mipmapping parameters (Section 2.2, Section 4.1). */
+typedef struct {
+    float iod_eta;     /* IoD threshold for ln(eta Ds) (paper: 1)                          */
+    float iod_chi;     /* IoD threshold for ln(chi Ds) (paper: 1)                          */
+    float chi_ds_min;  /* always average where the largest child chi * Ds is below this (0.25) */
+    int max_mip;       /* highest level, 0..4 (0: sparse skipping only)                   */
+    int log_mean;      /* 1: log-space (geometric) mean of the children; 0: box filter     */
+} dex_vlm_params;
+
+/*
+ * Build the MIP chains of every active block for each wavelength batch and
+ * select each block's level (Sections 2.1, 2.2, 2.3.1).
+ *   active, n_active  from dex_grid_build (device); capacity = host upper bound
+ *                     on n_active (grid size of the launch; bricks are sized by it)
+ *   params            host pointer
+ *   level_cap         device [nbz * nbx] per-block upper bound on the level, or NULL
+ *   bricks            device [n_batch][capacity][chain][2W] output records:
+ *                     level m of a block starts at record sum_{k<m} (16 >> k)^2 and
+ *                     is row-major over its (16 >> m)^2 voxels
+ *   state_words       device [n_batch][dex_state_words] output (zeroed by the call):
+ *                     block k's state (0 = empty, level + 1) in word k / 21, bits 3 (k % 21)
+ * The level of a block is the largest m <= max_mip such that every 2x2 group of
+ * every level 1..m inside it passes for every wavelength of the batch: both IoD
+ * values below their thresholds, or largest child chi * Ds < chi_ds_min.
+ */
+int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const float* eta, const float* chi,
+                   const int* active, const int* n_active, int capacity, const dex_vlm_params* params,
+                   const signed char* level_cap, float* bricks, unsigned long long* state_words);
+
+/*
+ * Accelerated formal solution (Section 2.3, Algorithm 1): the same long
+ * characteristics as dex_formal_solve_dense, from the centre of every cell of
+ * every active block, traversed with a hierarchical DDA that crosses empty
+ * blocks in one step and steps at each block's selected MIP level.
+ *   bricks, state_words, block_offset, active, n_active, capacity: from the calls above
+ *   J   device [n_lambda][nz][nx] output; zeroed by the call, written at probe cells
+ *   I   device [n_lambda][n_dir][nz][nx] output or NULL (zeroed by the call)
+ *   seg_count  device uint64 accumulator or NULL: adds the voxel segments integrated
+ */
+int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
+                          const unsigned long long* state_words, const int* block_offset, const int* active,
+                          const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
+                          float i_bc, float* J, float* I, unsigned long long* seg_count);
 
 #ifdef __cplusplus
 }

@@ -108,35 +108,44 @@ def _reduce(g, ds: float, mean: str):
 
 
 def mip_chain(eta, chi, max_mip: int, thr_eta: float, thr_chi: float,
-              chi_ds_min: float = 0.25, mean: str = "log"):
+              chi_ds_min: float = 0.25, mean: str = "log", stats: bool = False):
     """Levels 0..max_mip of (eta, chi) and the per-group pass flags of levels 1..max_mip.
 
     Returns ``(levels, passes)``: ``levels[m] = (eta_m, chi_m)`` of shape
     ``[L][nz >> m][nx >> m]``; ``passes[m - 1]`` is the bool pass map of level m.
+    With ``stats=True`` also a list of per-level dicts ``{"iod_eta", "iod_chi",
+    "chi_ds"}`` (the quantities each group's decision compares with its thresholds).
     """
     eta = np.asarray(eta, dtype=np.float64)
     chi = np.asarray(chi, dtype=np.float64)
     levels = [(eta, chi)]
     passes = []
+    st = []
     for m in range(1, max_mip + 1):
         ds = float(2 ** m)
         ge, gc = _groups(levels[-1][0]), _groups(levels[-1][1])
         ve, iod_e = _reduce(ge, ds, mean)
         vc, iod_c = _reduce(gc, ds, mean)
-        ok = ((iod_e < thr_eta) & (iod_c < thr_chi)) | (gc.max(-1) * ds < chi_ds_min)
+        kds = gc.max(-1) * ds
+        ok = ((iod_e < thr_eta) & (iod_c < thr_chi)) | (kds < chi_ds_min)
         levels.append((ve, vc))
         passes.append(ok)
-    return levels, passes
+        if stats:
+            st.append({"iod_eta": iod_e, "iod_chi": iod_c, "chi_ds": kds})
+    return (levels, passes, st) if stats else (levels, passes)
 
 
-def block_levels(passes, empty, block: int, lambda_batch: int):
+def block_levels(passes, empty, block: int, lambda_batch: int, level_cap=None, n_lambda: int | None = None):
     """[n_batch][nbz][nbx] int: the largest level whose groups (and all finer ones) pass
-    for every wavelength of the batch; -1 for empty blocks."""
+    for every wavelength of the batch, at most ``level_cap[bz][bx]`` when given; -1 for
+    empty blocks.  With no level above 0 (``passes == []``) every block is at level 0,
+    which needs ``n_lambda``."""
     empty = np.asarray(empty, dtype=bool)
     nbz, nbx = empty.shape
-    L = passes[0].shape[0] if passes else None
-    if L is None:
-        raise ValueError("need at least one MIP level above 0 (use block_levels_mip0)")
+    if not passes:
+        n_batch = -(-int(n_lambda) // lambda_batch)
+        return np.where(empty[None], -1, np.zeros((n_batch, nbz, nbx), dtype=np.int32))
+    L = passes[0].shape[0]
     n_batch = -(-L // lambda_batch)
     ok_all = np.ones((n_batch, nbz, nbx), dtype=bool)
     level = np.zeros((n_batch, nbz, nbx), dtype=np.int32)
@@ -147,6 +156,8 @@ def block_levels(passes, empty, block: int, lambda_batch: int):
                               for b in range(n_batch)])
         ok_all &= per_batch
         level = np.where(ok_all, m, level)
+    if level_cap is not None:
+        level = np.minimum(level, np.maximum(np.asarray(level_cap), 0)[None])
     level = np.where(empty[None], -1, level)
     return level
 

@@ -109,6 +109,7 @@ def formal_solve_dense(ctx: Context, nx: int, nz: int, n_lambda: int, W: int, pl
     d, w = _quadrature(dirs, weights)
     dev = planes.device
     n_probe = nx * nz if probes is None else int(probes.numel())
+    n_probe_arg = -1 if probes is None else n_probe
     if J is None:
         J = torch.empty((n_lambda, n_probe), dtype=torch.float32, device=dev)
     I = torch.empty((n_lambda, d.shape[0], n_probe), dtype=torch.float32, device=dev) if want_intensity else None
@@ -116,5 +117,129 @@ def formal_solve_dense(ctx: Context, nx: int, nz: int, n_lambda: int, W: int, pl
     fp = ctypes.POINTER(ctypes.c_float)
     ctx._rc(lib().dex_formal_solve_dense(
         ctx.handle, nx, nz, n_lambda, W, _ptr(planes), d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp),
-        n_probe, _ptr(probes), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+        n_probe_arg, _ptr(probes) if n_probe_arg > 0 else None, float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
     return J, I, seg
+
+
+# ------------------------------------------------------------ sparse path --
+
+BLOCK = 16
+STATES_PER_WORD = 21
+
+
+class VlmParams(ctypes.Structure):
+    """``dex_vlm_params``: variance-limited mipmapping thresholds (Section 2.2)."""
+    _fields_ = [("iod_eta", ctypes.c_float), ("iod_chi", ctypes.c_float), ("chi_ds_min", ctypes.c_float),
+                ("max_mip", ctypes.c_int), ("log_mean", ctypes.c_int)]
+
+
+class SparseGrid:
+    """Block sparsity map and Morton layout (device tensors) of an nx x nz grid."""
+
+    def __init__(self, nx, nz, block_offset, active, n_active):
+        self.nx, self.nz = nx, nz
+        self.nbx, self.nbz = nx // BLOCK, nz // BLOCK
+        self.block_offset = block_offset
+        self.active = active
+        self.n_active_dev = n_active
+
+    @property
+    def n_blocks(self):
+        return self.nbx * self.nbz
+
+    def n_active(self) -> int:
+        """Number of active blocks (synchronises)."""
+        return int(self.n_active_dev.item())
+
+
+class Mips:
+    """MIP chain bricks and packed block states of every wavelength batch."""
+
+    def __init__(self, bricks, words, W, max_mip, n_lambda, capacity):
+        self.bricks, self.words = bricks, words
+        self.W, self.max_mip, self.n_lambda, self.capacity = W, max_mip, n_lambda, capacity
+
+
+def synth_static_line(ctx: Context, chi_c, s_c, s_l, ratio, dld, dlam, eta=None, chi=None):
+    """MIP-0 eta, chi ``[n_lambda][n_cells]`` of the continuum + line model (``dex_synth_static_line``)."""
+    n_cells = chi_c.numel()
+    n_lambda = dlam.numel()
+    if eta is None:
+        eta = torch.empty((n_lambda, n_cells), dtype=torch.float32, device=chi_c.device)
+    if chi is None:
+        chi = torch.empty((n_lambda, n_cells), dtype=torch.float32, device=chi_c.device)
+    ctx._rc(lib().dex_synth_static_line(ctx.handle, n_cells, n_lambda, _ptr(chi_c), _ptr(s_c), _ptr(s_l),
+                                        _ptr(ratio), _ptr(dld), _ptr(dlam), _ptr(eta), _ptr(chi)))
+    return eta, chi
+
+
+def grid_build(ctx: Context, nx: int, nz: int, eta: torch.Tensor, chi: torch.Tensor, out: SparseGrid | None = None):
+    """Sparsity map + Morton-ordered active blocks (``dex_grid_build``); no synchronisation."""
+    n_lambda = eta.shape[0]
+    nb = (nx // BLOCK) * (nz // BLOCK)
+    if out is None:
+        dev = eta.device
+        out = SparseGrid(nx, nz, torch.empty(nb, dtype=torch.int32, device=dev),
+                         torch.zeros(nb, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.int32, device=dev))
+    ctx._rc(lib().dex_grid_build(ctx.handle, nx, nz, n_lambda, _ptr(eta), _ptr(chi), _ptr(out.block_offset),
+                                 _ptr(out.active), _ptr(out.n_active_dev)))
+    return out
+
+
+def state_words(nx: int, nz: int) -> int:
+    return int(lib().dex_state_words(nx, nz))
+
+
+def chain_voxels(max_mip: int) -> int:
+    return int(lib().dex_chain_voxels(max_mip))
+
+
+def mips_build(ctx: Context, grid: SparseGrid, eta, chi, W: int, max_mip: int, iod_eta: float, iod_chi: float,
+               chi_ds_min: float = 0.25, log_mean: bool = True, level_cap: torch.Tensor | None = None,
+               capacity: int | None = None, out: Mips | None = None):
+    """MIP chains + VLM block levels of every wavelength batch (``dex_mips_build``)."""
+    n_lambda = eta.shape[0]
+    cap = grid.n_blocks if capacity is None else int(capacity)
+    n_batch = -(-n_lambda // W)
+    if out is None:
+        nf = int(lib().dex_brick_floats(cap, n_lambda, W, max_mip))
+        bricks = torch.empty(max(nf, 1), dtype=torch.float32, device=eta.device)
+        words = torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=eta.device)
+        out = Mips(bricks, words, W, max_mip, n_lambda, cap)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 1 if log_mean else 0)
+    ctx._rc(lib().dex_mips_build(ctx.handle, grid.nx, grid.nz, n_lambda, W, _ptr(eta), _ptr(chi), _ptr(grid.active),
+                                 _ptr(grid.n_active_dev), cap, ctypes.byref(p), _ptr(level_cap), _ptr(out.bricks),
+                                 _ptr(out.words)))
+    return out
+
+
+def formal_solve_hdda(ctx: Context, grid: SparseGrid, mips: Mips, dirs, weights, i_bc: float = 0.0,
+                      want_intensity: bool = False, count_segments: bool = False, J: torch.Tensor | None = None):
+    """Accelerated (sparse + mipmapped) solve (``dex_formal_solve_hdda``).
+
+    Returns ``(J, I, seg)`` with dense ``J[n_lambda][nz*nx]`` (zero outside active blocks),
+    optional ``I[n_lambda][n_dir][nz*nx]`` and the integrated-segment count.
+    """
+    d, w = _quadrature(dirs, weights)
+    dev = mips.bricks.device
+    n_cells = grid.nx * grid.nz
+    if J is None:
+        J = torch.empty((mips.n_lambda, n_cells), dtype=torch.float32, device=dev)
+    I = torch.empty((mips.n_lambda, d.shape[0], n_cells), dtype=torch.float32, device=dev) if want_intensity else None
+    seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
+    fp = ctypes.POINTER(ctypes.c_float)
+    ctx._rc(lib().dex_formal_solve_hdda(
+        ctx.handle, grid.nx, grid.nz, mips.n_lambda, mips.W, mips.max_mip, _ptr(mips.bricks), _ptr(mips.words),
+        _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev), mips.capacity, d.shape[0],
+        d.ctypes.data_as(fp), w.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+    return J, I, seg
+
+
+def unpack_states(words: np.ndarray, n_blocks: int) -> np.ndarray:
+    """Host-side decode of packed block states into levels (-1 = empty), for inspection."""
+    w = np.asarray(words).astype(np.uint64).reshape(-1, words.shape[-1])
+    out = np.empty((w.shape[0], n_blocks), dtype=np.int32)
+    k = np.arange(n_blocks)
+    for b in range(w.shape[0]):
+        out[b] = ((w[b][k // STATES_PER_WORD] >> (3 * (k % STATES_PER_WORD)).astype(np.uint64)) & 7).astype(np.int32) - 1
+    return out

@@ -179,8 +179,13 @@ int dex_formal_solve_dense(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, co
     if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
     if (n_lambda < 0) return fail(ctx, DEX_ERR_ARG, "negative n_lambda");
     const long long n_cells = (long long)nx * nz;
-    if (!probes) n_probe = (int)std::min<long long>(n_cells, 0x7fffffff);
-    if (n_probe < 0) return fail(ctx, DEX_ERR_ARG, "negative n_probe");
+    if (n_probe < 0) {  // every cell is a probe
+        if (probes) return fail(ctx, DEX_ERR_ARG, "n_probe < 0 (every cell) takes no probe list");
+        if (n_cells > 0x7fffffffLL) return fail(ctx, DEX_ERR_ARG, "grid too large for an all-cell solve");
+        n_probe = (int)n_cells;
+    } else if (n_probe > 0 && !probes) {
+        return fail(ctx, DEX_ERR_ARG, "probe list required for n_probe > 0");
+    }
     if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
     dex::DenseParams P{};
     if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
@@ -204,6 +209,161 @@ int dex_formal_solve_dense(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, co
     if (int r = bind(ctx)) return r;
     cudaError_t e = dex::launch_solve_dense(ctx->stream, P);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_dense launch");
+    return ok(ctx);
+}
+
+int dex_synth_static_line(dex_ctx* ctx, int n_cells, int n_lambda, const float* chi_c, const float* s_c,
+                          const float* s_l, const float* ratio, const float* dld, const float* dlam, float* eta,
+                          float* chi)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (n_cells < 0 || n_lambda < 0) return fail(ctx, DEX_ERR_ARG, "negative size");
+    if (n_cells == 0 || n_lambda == 0) return ok(ctx);
+    if (!chi_c || !s_c || !s_l || !ratio || !dld || !dlam || !eta || !chi)
+        return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_synth_static_line(ctx->stream, n_cells, n_lambda, chi_c, s_c, s_l, ratio, dld,
+                                                  dlam, eta, chi);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "synth_static_line launch");
+    return ok(ctx);
+}
+
+static int check_sparse_grid(dex_ctx* ctx, int nx, int nz)
+{
+    if (nx < DEX_BLOCK || nz < DEX_BLOCK || nx % DEX_BLOCK || nz % DEX_BLOCK)
+        return fail(ctx, DEX_ERR_ARG, "sparse grids need nx, nz positive multiples of %d, got %d x %d", DEX_BLOCK,
+                    nx, nz);
+    const long long nb = (long long)(nx / DEX_BLOCK) * (nz / DEX_BLOCK);
+    if (nb > (long long)DEX_STATES_PER_WORD * 24576 || nx > 65536 || nz > 65536)
+        return fail(ctx, DEX_ERR_ARG, "sparse grid too large (%lld blocks)", nb);
+    return DEX_OK;
+}
+
+size_t dex_state_words(int nx, int nz)
+{
+    if (nx < DEX_BLOCK || nz < DEX_BLOCK) return 0;
+    const size_t nb = (size_t)(nx / DEX_BLOCK) * (size_t)(nz / DEX_BLOCK);
+    return (nb + DEX_STATES_PER_WORD - 1) / DEX_STATES_PER_WORD;
+}
+
+int dex_chain_voxels(int max_mip)
+{
+    if (max_mip < 0 || max_mip > 4) return 0;
+    return dex::chain_length(max_mip);
+}
+
+size_t dex_brick_floats(int capacity, int n_lambda, int W, int max_mip)
+{
+    if (capacity < 0 || n_lambda < 0 || !valid_W(W) || max_mip < 0 || max_mip > 4) return 0;
+    const size_t n_batch = (size_t)((n_lambda + W - 1) / W);
+    return n_batch * (size_t)capacity * (size_t)dex::chain_length(max_mip) * (size_t)(2 * W);
+}
+
+int dex_grid_build(dex_ctx* ctx, int nx, int nz, int n_lambda, const float* eta, const float* chi,
+                   int* block_offset, int* active, int* n_active)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_sparse_grid(ctx, nx, nz)) return r;
+    if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
+    if (!eta || !chi || !block_offset || !active || !n_active) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_grid_build(ctx->stream, nx, nz, n_lambda, eta, chi, block_offset, active, n_active);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "grid_build launch");
+    return ok(ctx);
+}
+
+int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const float* eta, const float* chi,
+                   const int* active, const int* n_active, int capacity, const dex_vlm_params* params,
+                   const signed char* level_cap, float* bricks, unsigned long long* state_words)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_sparse_grid(ctx, nx, nz)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
+    if (!params) return fail(ctx, DEX_ERR_ARG, "params required");
+    if (params->max_mip < 0 || params->max_mip > 4)
+        return fail(ctx, DEX_ERR_ARG, "max_mip must be in [0, 4], got %d", params->max_mip);
+    if (std::isnan(params->iod_eta) || std::isnan(params->iod_chi) || std::isnan(params->chi_ds_min))
+        return fail(ctx, DEX_ERR_ARG, "NaN threshold");
+    const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
+    if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
+    if (!eta || !chi || !active || !n_active || !bricks || !state_words) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    dex::MipParams P{};
+    P.nx = nx;
+    P.nz = nz;
+    P.nbx = nx / DEX_BLOCK;
+    P.nbz = nz / DEX_BLOCK;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.max_mip = params->max_mip;
+    P.chain = dex::chain_length(params->max_mip);
+    P.n_words = (int)dex_state_words(nx, nz);
+    P.cap_active = capacity;
+    P.log_mean = params->log_mean != 0;
+    P.thr_eta = params->iod_eta;
+    P.thr_chi = params->iod_chi;
+    P.chi_ds_min = params->chi_ds_min;
+    P.eta = eta;
+    P.chi = chi;
+    P.active = active;
+    P.n_active = n_active;
+    P.level_cap = level_cap;
+    P.bricks = bricks;
+    P.words = state_words;
+    P.status = ctx->status;
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_mips_build(ctx->stream, P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mips_build launch");
+    return ok(ctx);
+}
+
+int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
+                          const unsigned long long* state_words, const int* block_offset, const int* active,
+                          const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
+                          float i_bc, float* J, float* I, unsigned long long* seg_count)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_sparse_grid(ctx, nx, nz)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
+    if (max_mip < 0 || max_mip > 4) return fail(ctx, DEX_ERR_ARG, "max_mip must be in [0, 4]");
+    const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
+    if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
+    if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
+    dex::HddaParams P{};
+    if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
+    if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
+        return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    P.nx = nx;
+    P.nz = nz;
+    P.nbx = nx / DEX_BLOCK;
+    P.nbz = nz / DEX_BLOCK;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.chain = dex::chain_length(max_mip);
+    P.n_words = (int)dex_state_words(nx, nz);
+    P.cap_active = capacity;
+    P.n_cells = (long long)nx * nz;
+    P.bricks = bricks;
+    P.words = state_words;
+    P.block_offset = block_offset;
+    P.active = active;
+    P.n_active = n_active;
+    P.i_bc = i_bc;
+    P.J = J;
+    P.I = I;
+    P.seg_count = seg_count;
+    P.status = ctx->status;
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
+    if (e == cudaSuccess && I)
+        e = cudaMemsetAsync(I, 0, sizeof(float) * (size_t)n_lambda * (size_t)n_dir * (size_t)P.n_cells, ctx->stream);
+    if (e == cudaSuccess) e = dex::launch_solve_hdda(ctx->stream, P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_hdda launch");
     return ok(ctx);
 }
 

@@ -60,6 +60,38 @@ __device__ __forceinline__ void segment(float S, float chi, float nl2, float len
     T *= e;
 }
 
+// Ray parameter of grid planes as an unevaluated sum hi + lo of two floats.
+// A plane at offset P (a half-integer, exact) from the origin along an axis
+// with direction component d is hit at t = P / d.  hi = P * ih is the rounded
+// product with ih = fl(1/d); lo collects the product's rounding error (exact
+// through an FMA) plus P times the residual 1/d - ih.  Path lengths are then
+// differences (hi_b - hi_a) + (lo_b - lo_a), accurate relative to the length
+// itself rather than to t, which matters far from the origin (t ~ 1e3 cells has
+// an fp32 ulp of ~1e-4 cell).
+struct AxisParam {
+    float ih;  // fl(1/d), +inf for d == 0
+    float il;  // 1/d - ih
+};
+
+__device__ __forceinline__ AxisParam axis_param(float d)
+{
+    AxisParam a;
+    if (d != 0.0f) {
+        a.ih = 1.0f / d;
+        a.il = fmaf(-d, a.ih, 1.0f) * a.ih;
+    } else {
+        a.ih = __int_as_float(0x7f800000);
+        a.il = 0.0f;
+    }
+    return a;
+}
+
+// lo part of the parameter of plane P whose rounded value is hi = P * a.ih
+__device__ __forceinline__ float plane_lo(float P, const AxisParam& a, float hi)
+{
+    return fmaf(P, a.il, fmaf(P, a.ih, -hi));
+}
+
 // Loads of one wavelength-batch record (2W floats, 8W-byte aligned).
 template <int W>
 struct Record {

@@ -22,6 +22,45 @@ struct DenseParams {
     Quadrature quad;
 };
 
+struct MipParams {
+    int nx, nz, nbx, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active;
+    bool log_mean;
+    float thr_eta, thr_chi, chi_ds_min;
+    const float* eta;
+    const float* chi;
+    const int* active;
+    const int* n_active;
+    const signed char* level_cap;
+    float* bricks;
+    unsigned long long* words;
+    unsigned int* status;
+};
+
+struct HddaParams {
+    int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active;
+    long long n_cells;
+    const float* bricks;
+    const unsigned long long* words;
+    const int* block_offset;
+    const int* active;
+    const int* n_active;
+    float i_bc;
+    float* J;
+    float* I;
+    unsigned long long* seg_count;
+    unsigned int* status;
+    Quadrature quad;
+};
+
+int chain_length(int max_mip);
+cudaError_t launch_synth_static_line(cudaStream_t s, long long n_cells, int n_lambda, const float* chi_c,
+                                     const float* s_c, const float* s_l, const float* ratio, const float* dld,
+                                     const float* dlam, float* eta, float* chi);
+cudaError_t launch_grid_build(cudaStream_t s, int nx, int nz, int n_lambda, const float* eta, const float* chi,
+                              int* block_offset, int* active, int* n_active);
+cudaError_t launch_mips_build(cudaStream_t s, const MipParams& p);
+cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& p);
+
 cudaError_t launch_pack_planes(cudaStream_t s, long long n_cells, int n_lambda, int W,
                                const float* eta, const float* chi, float* planes, unsigned int* status);
 cudaError_t launch_solve_dense(cudaStream_t s, const DenseParams& p);

@@ -56,10 +56,9 @@ __global__ void k_pack_planes(long long n_cells, int n_lambda, int W, int n_batc
 template <int W>
 __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
 {
-    const float kInf = __int_as_float(0x7f800000);
     const int b = blockIdx.y;
     int i, j, p;
-    if (P.probes == nullptr) {
+    if (P.probes == nullptr) {  // every cell is a probe
         // 32 x 8 tile of probes per CTA: lanes along x, warps along z
         const int tiles_x = (P.nx + 31) >> 5;
         const int tx = blockIdx.x % tiles_x, tz = blockIdx.x / tiles_x;
@@ -89,25 +88,28 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
 
     for (int k = 0; k < P.quad.n_dir; ++k) {
         const float dx = P.quad.dx[k], dz = P.quad.dz[k];
-        const int sx = dx > 0.0f ? 1 : -1, sz = dz > 0.0f ? 1 : -1;
-        const float hx = dx < 0.0f ? -0.5f : 0.5f, hz = dz < 0.0f ? -0.5f : 0.5f;
-        const float idx = dx != 0.0f ? 1.0f / dx : kInf;
-        const float idz = dz != 0.0f ? 1.0f / dz : kInf;
-        const float t2x = dx != 0.0f ? ((float)(dx > 0.0f ? P.nx - 1 - i : -i) + hx) * idx : kInf;
-        const float t2z = dz != 0.0f ? ((float)(dz > 0.0f ? P.nz - 1 - j : -j) + hz) * idz : kInf;
-        const float t2 = fminf(t2x, t2z);
+        // a zero component counts as positive, so its plane offsets are positive
+        // and their parameters (offset * inf) are +inf: that axis never steps
+        const int sx = dx < 0.0f ? -1 : 1, sz = dz < 0.0f ? -1 : 1;
+        const AxisParam ax = axis_param(dx), az = axis_param(dz);
+        // plane offsets from the origin (half-integers, exact): next plane, exit plane
+        float Px = dx < 0.0f ? -0.5f : 0.5f, Pz = dz < 0.0f ? -0.5f : 0.5f;
+        const float Ex = dx < 0.0f ? (float)(-i) - 0.5f : (float)(P.nx - i) - 0.5f;
+        const float Ez = dz < 0.0f ? (float)(-j) - 0.5f : (float)(P.nz - j) - 0.5f;
+        const float t2 = fminf(Ex * ax.ih, Ez * az.ih);
 
         int di = 0, dj = 0;
-        float t = 0.0f;
+        float th_prev = 0.0f, tl_prev = 0.0f;
         float I[W], T[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
 
         for (int it = 0;; ++it) {
-            const float tnx = ((float)di + hx) * idx;
-            const float tnz = ((float)dj + hz) * idz;
-            const float th = fminf(fminf(tnx, tnz), t2);
-            const float len = th - t;
+            const float tnx = Px * ax.ih, tnz = Pz * az.ih;
+            const bool on_x = tnx <= tnz;
+            const float th = on_x ? tnx : tnz;
+            const float tl = plane_lo(on_x ? Px : Pz, on_x ? ax : az, th);
+            const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
             const int ci = i + di, cj = j + dj;
             if (it >= cap || (unsigned)ci >= (unsigned)P.nx || (unsigned)cj >= (unsigned)P.nz) {
                 capped = true;
@@ -117,10 +119,11 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
             const float nl2 = len * kNegLog2e;
 #pragma unroll
             for (int w = 0; w < W; ++w) segment(r.S[w], r.chi[w], nl2, len, I[w], T[w]);
-            nseg += (len > 0.0f);
-            t = th;
+            nseg += (th > th_prev);
+            th_prev = th;
+            tl_prev = tl;
             if (th >= t2) break;
-            if (tnx <= tnz) di += sx; else dj += sz;
+            if (on_x) { di += sx; Px += (float)sx; } else { dj += sz; Pz += (float)sz; }
         }
         const float wk = P.quad.w[k];
 #pragma unroll
