@@ -55,7 +55,15 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--nx", type=int, default=1024, help="grid side (smaller sides for profiling captures)")
+    ap.add_argument("--phase", default="all", choices=["all", "accel", "plain"],
+                    help="accel/plain: time only that path (profiling captures)")
+    args = ap.parse_args()
+    global NX, NZ, WORKLOAD
+    if args.nx != NX:
+        NX = NZ = args.nx
+        WORKLOAD = WORKLOAD.replace("1024x1024", f"{NX}x{NZ}")
+    return args
 
 
 def dist_env():
@@ -161,7 +169,7 @@ class Workload:
         self.synth()
         self.grid = api.grid_build(self.ctx, NX, NZ, self.eta, self.chi, out=self.grid)
         self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, W, MAX_MIP, thr, thr, CHI_DS_MIN,
-                                   out=self.mips)
+                                   log_mean=False, out=self.mips)
         if ev is not None:
             ev[0].record()
         _, _, seg = api.formal_solve_hdda(self.ctx, self.grid, self.mips, self.dirs, self.w, J=self.J,
@@ -213,6 +221,20 @@ def native(args):
 
     def flush():
         l2_flush(flush_buf)
+
+    if args.phase != "all":  # profiling capture: only the requested path, no report
+        if args.phase == "accel":
+            time_steps(lambda ev: wl.step(ev=ev), args.steps, args.warmup, torch, flush)
+        else:
+            wl.step()
+            probes = wl.probes()
+            planes = api.pack_planes(ctx, wl.eta, wl.chi, W)
+            time_steps(lambda ev: (ev[0].record() if ev else None,
+                                   api.formal_solve_dense(ctx, NX, NZ, N_LAMBDA, W, planes, wl.dirs, wl.w,
+                                                          probes=probes),
+                                   ev[1].record() if ev else None), args.steps, args.warmup, torch, flush)
+        ctx.check()
+        return
 
     # --- untimed: dense-equivalent segment count, plain reference J, executed segment counts
     seg_acc = wl.step(count=True)

@@ -85,15 +85,18 @@ const char* dex_last_error(const dex_ctx* ctx);
  * a batch width W (1, 2, 4 or 8) and n_batch = ceil(n_lambda / W) batches,
  *     planes[b][c][0 .. W-1]   = S (source function) of wavelengths b*W + w
  *     planes[b][c][W .. 2W-1]  = chi of the same wavelengths
- * with S = eta / chi where chi > 0 and S = eta where chi == 0 (a transparent
- * emitter; the solvers then add eta * length).  Wavelengths beyond n_lambda
- * are zero.  One record is 8*W bytes, so a W = 8 record is one 64-byte unit.
+ * with S = eta / chi where chi > 0.  A transparent emitter (chi = 0, eta > 0)
+ * is stored as chi = eta * 2^-60, S = 2^60, which adds eta * length to the
+ * intensity to float32 precision for eta <= 2^36 (larger values are rejected
+ * with DEX_ERR_NUMERIC).  eta = chi = 0 is stored as S = chi = 0.  Wavelengths
+ * beyond n_lambda are zero.  One record is 8*W bytes (W = 8: one 64-byte unit).
  */
 
 /*
  * Pack eta, chi ([n_lambda][n_cells] float32, device) into planes
  * ([n_batch][n_cells][2W] float32, device).  A negative or non-finite chi or
- * eta sets DEX_ERR_NUMERIC in the device status word (the value is stored as 0).
+ * eta, or a transparent emitter above 2^36, sets DEX_ERR_NUMERIC in the device
+ * status word (the voxel is stored as empty).
  */
 int dex_pack_planes(dex_ctx* ctx, int n_cells, int n_lambda, int W,
                     const float* eta, const float* chi, float* planes);
@@ -209,6 +212,11 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
  * every active block, traversed with a hierarchical DDA that crosses empty
  * blocks in one step and steps at each block's selected MIP level.
  *   bricks, state_words, block_offset, active, n_active, capacity: from the calls above
+ *   n_band, band  host [n_band] (n_band <= 4) non-decreasing distances, or band = NULL
+ *       for no limit: a block first entered at ray parameter t is sampled at level
+ *       min(selected level, #{m : band[m-1] <= t}), the long-characteristics form of
+ *       the per-cascade maximum MIP level of Section 4.1 (full resolution near the
+ *       probe, coarser levels only further out; n_band = 0 forces level 0)
  *   J   device [n_lambda][nz][nx] output; zeroed by the call, written at probe cells
  *   I   device [n_lambda][n_dir][nz][nx] output or NULL (zeroed by the call)
  *   seg_count  device uint64 accumulator or NULL: adds the voxel segments integrated
@@ -216,7 +224,69 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
 int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
                           const unsigned long long* state_words, const int* block_offset, const int* active,
                           const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
-                          float i_bc, float* J, float* I, unsigned long long* seg_count);
+                          int n_band, const float* band, float i_bc, float* J, float* I,
+                          unsigned long long* seg_count);
+
+/* ------------------------------------------------ level populations (SE) --
+ *
+ * A multi-level atom with radiative lines and collisional coupling (cgs units).
+ * Populations are float64 [n_level][n_cells]; temperature, electron and
+ * hydrogen densities float32 [n_cells] (T <= 0 marks an empty cell: zero
+ * populations, zero emissivity/opacity).  Wavelength samples are host arrays:
+ * lambda_nm[n_lambda] and line_tag[n_lambda] (index of the line a sample
+ * belongs to, or -1 for a background-only sample); n_lambda <= DEX_MAX_ATOM_LAMBDA.
+ */
+#define DEX_MAX_LEVELS 4
+#define DEX_MAX_LINES 4
+#define DEX_MAX_ATOM_LAMBDA 256
+
+typedef struct {
+    int n_level;                                  /* <= DEX_MAX_LEVELS                      */
+    double energy_erg[DEX_MAX_LEVELS];            /* level energies above the ground level  */
+    double g[DEX_MAX_LEVELS];                     /* statistical weights                    */
+    int n_line;                                   /* <= DEX_MAX_LINES                       */
+    int line_lower[DEX_MAX_LINES];
+    int line_upper[DEX_MAX_LINES];
+    double line_A[DEX_MAX_LINES];                 /* Einstein A_ul (1/s)                    */
+    double line_lambda0_nm[DEX_MAX_LINES];        /* rest wavelengths                       */
+    double upsilon[DEX_MAX_LEVELS][DEX_MAX_LEVELS]; /* collision strengths, [i][j] with i < j */
+    double mass_amu;                              /* atomic mass (Doppler widths)           */
+    double background_sigma;                      /* grey background opacity per electron (cm^2) */
+    double cell_cm;                               /* voxel side: eta, chi are per voxel     */
+} dex_atom;
+
+/* Boltzmann (LTE) populations summing to n_H: the iteration's starting point. */
+int dex_lte_populations(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature,
+                        const float* nh, double* pops);
+
+/*
+ * Section 2, Eqs. Eta and Chi (complete redistribution) for every line, plus a
+ * grey background chi_c = background_sigma n_e with Planck source function:
+ *   eta = (h nu / 4 pi) n_u A_ul phi(nu),  chi = (h nu / 4 pi)(n_l B_lu - n_u B_ul) phi(nu),
+ * B_ul = A_ul c^2 / (2 h nu0^3), B_lu = (g_u / g_l) B_ul, phi a Doppler profile
+ * (width nu0/c sqrt(2kT/m)) renormalised to unit trapezoid quadrature over the
+ * line's samples.  Outputs float32 [n_lambda][n_cells], per voxel (x cell_cm).
+ */
+int dex_atom_eta_chi(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_lambda, const double* lambda_nm,
+                     const int* line_tag, const float* temperature, const float* ne, const double* pops,
+                     float* eta, float* chi);
+
+/*
+ * Radiative-rate reduction: Jbar[l][c] = sum_k w_k phi_k(c) J[k][c] over line l's
+ * samples (trapezoid weights in frequency, the same renormalised profile), in
+ * float64.  J: float32 [n_lambda][n_cells]; jbar: float64 [n_line][n_cells].
+ */
+int dex_rates_accumulate(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_lambda, const double* lambda_nm,
+                         const int* line_tag, const float* temperature, const float* J, double* jbar);
+
+/*
+ * Per-cell statistical equilibrium in float64: rates R_lu = B_lu Jbar,
+ * R_ul = A_ul + B_ul Jbar, collisional C_ij = n_e 8.629e-6 / (g_i sqrt T) Upsilon_ij
+ * e^{-dE/kT} (i < j) with detailed balance for C_ji; sum_j n_j P_ji = n_i sum_j P_ij,
+ * the ground-level equation replaced by sum_i n_i = n_H.  pops: float64 output.
+ */
+int dex_se_solve(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature, const float* ne,
+                 const float* nh, const double* jbar, double* pops);
 
 #ifdef __cplusplus
 }

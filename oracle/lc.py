@@ -51,6 +51,10 @@ def lib():
             L.oracle_formal_solve.restype = ctypes.c_int
             L.oracle_formal_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_int,
                                               dp, dp, ctypes.c_int, ip, ctypes.c_double, dp, dp]
+            L.oracle_formal_solve_banded.restype = ctypes.c_int
+            L.oracle_formal_solve_banded.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ip,
+                                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, dp, dp,
+                                                     ctypes.c_int, ip, ctypes.c_double, dp, dp]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_num_threads.argtypes = []
             _lib = L
@@ -113,4 +117,36 @@ def formal_solve(eta, chi, dirs, weights, probes=None, i_bc: float = 0.0, want_i
                                    _dptr(I) if I is not None else ctypes.POINTER(ctypes.c_double)())
     if rc != 0:
         raise RuntimeError("oracle formal solve failed")
+    return (J, I) if want_intensity else J
+
+
+def formal_solve_banded(levels, level_map, block: int, lambda_batch: int, band, dirs, weights, probes,
+                        i_bc: float = 0.0, want_intensity: bool = False):
+    """Formal solution over MIP levels with a distance-limited level per block visit.
+
+    levels: list of (eta_m, chi_m) ``[L][nz >> m][nx >> m]`` (as from ``mips.mip_chain``);
+    level_map: ``[n_batch][nbz][nbx]``; band: thresholds d_1 <= d_2 <= ... (level m allowed
+    in blocks entered at t >= d_m).  Returns J (and I) like :func:`formal_solve`.
+    """
+    L, nz, nx = levels[0][0].shape
+    n_lev = len(levels)
+    le = np.empty((n_lev, L, nz, nx))
+    lch = np.empty((n_lev, L, nz, nx))
+    for m, (em, cm) in enumerate(levels):
+        f = 2 ** m
+        le[m] = np.repeat(np.repeat(em, f, axis=1), f, axis=2)
+        lch[m] = np.repeat(np.repeat(cm, f, axis=1), f, axis=2)
+    lm = np.ascontiguousarray(np.asarray(level_map, dtype=np.int32))
+    b = np.ascontiguousarray(np.asarray(band, dtype=np.float64).reshape(-1))
+    d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 2))
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    p = np.ascontiguousarray(np.asarray(probes, dtype=np.int32))
+    J = np.zeros((L, p.size))
+    I = np.zeros((L, d.shape[0], p.size)) if want_intensity else None
+    rc = lib().oracle_formal_solve_banded(nx, nz, L, n_lev, _dptr(le), _dptr(lch), _iptr(lm), block, lambda_batch,
+                                          b.size, _dptr(b) if b.size else ctypes.POINTER(ctypes.c_double)(),
+                                          d.shape[0], _dptr(d), _dptr(w), p.size, _iptr(p), float(i_bc), _dptr(J),
+                                          _dptr(I) if I is not None else ctypes.POINTER(ctypes.c_double)())
+    if rc != 0:
+        raise RuntimeError("oracle banded formal solve failed")
     return (J, I) if want_intensity else J

@@ -195,3 +195,86 @@ int oracle_num_threads(void)
 #endif
     return n;
 }
+
+/*
+ * Formal solution over a mipmapped grid with a distance-limited level per
+ * block visit (Section 4.1: each radiance-cascade interval samples at most a
+ * given MIP level, full resolution near the probe and coarser far away; here
+ * the long-characteristics form: a block first entered at ray parameter t is
+ * sampled at level min(L_block, m_max(t)), m_max(t) = number of thresholds
+ * band[m-1] <= t for m = 1..n_band).
+ *   lev_eta, lev_chi : [n_lev][n_lambda][nz][nx]; entry [m][l][c] is the value of
+ *                      the level-m voxel containing cell c (level 0 = the cell)
+ *   block_level      : [n_batch][nbz][nbx] selected level (-1 = empty block)
+ *   block, lambda_batch : block side and wavelengths per level map
+ * Other arguments as oracle_formal_solve.  Returns 0 or -1.
+ */
+int oracle_formal_solve_banded(int nx, int nz, int n_lambda, int n_lev, const double* lev_eta,
+                               const double* lev_chi, const int* block_level, int block, int lambda_batch,
+                               int n_band, const double* band, int n_dir, const double* dirs,
+                               const double* weights, int n_probe, const int* probes, double i_bc,
+                               double* J, double* I)
+{
+    int cap = 2 * (nx + nz) + 8;
+    size_t plane = (size_t)nx * (size_t)nz;
+    int nbx = nx / block, nbz = nz / block;
+    int err = 0;
+#pragma omp parallel
+    {
+        int* cell = (int*)malloc(sizeof(int) * (size_t)cap);
+        double* len = (double*)malloc(sizeof(double) * (size_t)cap);
+        int* mcap = (int*)malloc(sizeof(int) * (size_t)cap);
+#pragma omp for schedule(dynamic, 16)
+        for (int p = 0; p < n_probe; ++p) {
+            int c = probes[p];
+            double ox = (double)(c % nx) + 0.5, oz = (double)(c / nx) + 0.5;
+            for (int l = 0; l < n_lambda; ++l) J[(size_t)l * n_probe + p] = 0.0;
+            for (int k = 0; k < n_dir; ++k) {
+                int ns = oracle_ray_segments(nx, nz, ox, oz, dirs[2 * k], dirs[2 * k + 1], cap, cell, len);
+                if (ns < 0) {
+#pragma omp atomic write
+                    err = 1;
+                    ns = 0;
+                }
+                /* distance cap of each piece: from the parameter at which its block was entered */
+                double t = 0.0, t_entry = 0.0;
+                int prev_blk = -1;
+                for (int s = 0; s < ns; ++s) {
+                    int bi = (cell[s] % nx) / block, bj = (cell[s] / nx) / block;
+                    int blk = bj * nbx + bi;
+                    if (blk != prev_blk) { t_entry = t; prev_blk = blk; }
+                    int m = 0;
+                    while (m < n_band && band[m] <= t_entry) ++m;
+                    mcap[s] = m;
+                    t += len[s];
+                }
+                for (int l = 0; l < n_lambda; ++l) {
+                    const int* lmap = block_level + (size_t)(l / lambda_batch) * nbx * nbz;
+                    double inten = i_bc;
+                    for (int s = ns - 1; s >= 0; --s) {
+                        int bi = (cell[s] % nx) / block, bj = (cell[s] / nx) / block;
+                        int L = lmap[bj * nbx + bi];
+                        if (L < 0) continue; /* empty block: eta = chi = 0 */
+                        int m = L < mcap[s] ? L : mcap[s];
+                        if (m >= n_lev) m = n_lev - 1;
+                        size_t off = ((size_t)m * n_lambda + l) * plane + (size_t)cell[s];
+                        double x = lev_chi[off], e = lev_eta[off];
+                        if (x > 0.0) {
+                            double tau = x * len[s];
+                            inten = inten * exp(-tau) + (e / x) * (-expm1(-tau));
+                        } else {
+                            inten = inten + e * len[s];
+                        }
+                    }
+                    J[(size_t)l * n_probe + p] += weights[k] * inten;
+                    if (I) I[((size_t)l * n_dir + k) * n_probe + p] = inten;
+                }
+            }
+        }
+        free(cell);
+        free(len);
+        free(mcap);
+    }
+    (void)nbz;
+    return err ? -1 : 0;
+}

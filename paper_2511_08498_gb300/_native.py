@@ -40,8 +40,13 @@ PROTOTYPES = {
     "dex_mips_build": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                c_void_p, c_void_p, c_void_p, c_void_p]),
     "dex_formal_solve_hdda": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
-                                      c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_float, c_void_p, c_void_p,
-                                      c_void_p]),
+                                      c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float, c_void_p,
+                                      c_void_p, c_void_p]),
+    "dex_lte_populations": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "dex_atom_eta_chi": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p] + [c_void_p] * 5),
+    "dex_rates_accumulate": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
+                                     c_void_p]),
+    "dex_se_solve": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 5),
 }
 
 

@@ -195,7 +195,7 @@ def chain_voxels(max_mip: int) -> int:
 
 
 def mips_build(ctx: Context, grid: SparseGrid, eta, chi, W: int, max_mip: int, iod_eta: float, iod_chi: float,
-               chi_ds_min: float = 0.25, log_mean: bool = True, level_cap: torch.Tensor | None = None,
+               chi_ds_min: float = 0.25, log_mean: bool = False, level_cap: torch.Tensor | None = None,
                capacity: int | None = None, out: Mips | None = None):
     """MIP chains + VLM block levels of every wavelength batch (``dex_mips_build``)."""
     n_lambda = eta.shape[0]
@@ -214,8 +214,12 @@ def mips_build(ctx: Context, grid: SparseGrid, eta, chi, W: int, max_mip: int, i
 
 
 def formal_solve_hdda(ctx: Context, grid: SparseGrid, mips: Mips, dirs, weights, i_bc: float = 0.0,
-                      want_intensity: bool = False, count_segments: bool = False, J: torch.Tensor | None = None):
+                      want_intensity: bool = False, count_segments: bool = False, J: torch.Tensor | None = None,
+                      band=None):
     """Accelerated (sparse + mipmapped) solve (``dex_formal_solve_hdda``).
+
+    ``band``: optional non-decreasing distances (at most 4); level m is used only in
+    blocks first entered at ray parameter t >= band[m-1].
 
     Returns ``(J, I, seg)`` with dense ``J[n_lambda][nz*nx]`` (zero outside active blocks),
     optional ``I[n_lambda][n_dir][nz*nx]`` and the integrated-segment count.
@@ -228,10 +232,12 @@ def formal_solve_hdda(ctx: Context, grid: SparseGrid, mips: Mips, dirs, weights,
     I = torch.empty((mips.n_lambda, d.shape[0], n_cells), dtype=torch.float32, device=dev) if want_intensity else None
     seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
     fp = ctypes.POINTER(ctypes.c_float)
+    b = None if band is None else _host_f32(band).reshape(-1)
     ctx._rc(lib().dex_formal_solve_hdda(
         ctx.handle, grid.nx, grid.nz, mips.n_lambda, mips.W, mips.max_mip, _ptr(mips.bricks), _ptr(mips.words),
         _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev), mips.capacity, d.shape[0],
-        d.ctypes.data_as(fp), w.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+        d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
+        None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
     return J, I, seg
 
 
@@ -243,3 +249,121 @@ def unpack_states(words: np.ndarray, n_blocks: int) -> np.ndarray:
     for b in range(w.shape[0]):
         out[b] = ((w[b][k // STATES_PER_WORD] >> (3 * (k % STATES_PER_WORD)).astype(np.uint64)) & 7).astype(np.int32) - 1
     return out
+
+
+# ---------------------------------------------------- level populations --
+
+MAX_LEVELS, MAX_LINES = 4, 4
+
+
+class Atom(ctypes.Structure):
+    """``dex_atom``: levels, radiative lines and collision strengths (cgs)."""
+    _fields_ = [("n_level", ctypes.c_int), ("energy_erg", ctypes.c_double * MAX_LEVELS),
+                ("g", ctypes.c_double * MAX_LEVELS), ("n_line", ctypes.c_int),
+                ("line_lower", ctypes.c_int * MAX_LINES), ("line_upper", ctypes.c_int * MAX_LINES),
+                ("line_A", ctypes.c_double * MAX_LINES), ("line_lambda0_nm", ctypes.c_double * MAX_LINES),
+                ("upsilon", (ctypes.c_double * MAX_LEVELS) * MAX_LEVELS), ("mass_amu", ctypes.c_double),
+                ("background_sigma", ctypes.c_double), ("cell_cm", ctypes.c_double)]
+
+    @classmethod
+    def from_dict(cls, d, cell_cm: float, background_sigma: float = 6.652e-25):
+        a = cls()
+        ev = 1.602176634e-12
+        a.n_level = len(d["g"])
+        for i, (E, g) in enumerate(zip(d["energy_ev"], d["g"])):
+            a.energy_erg[i] = float(E) * ev
+            a.g[i] = float(g)
+        a.n_line = len(d["lines"])
+        for l, (lo, up, A, lam0) in enumerate(d["lines"]):
+            a.line_lower[l], a.line_upper[l], a.line_A[l], a.line_lambda0_nm[l] = lo, up, A, lam0
+        for (i, j), u in d["upsilon"].items():
+            a.upsilon[i][j] = float(u)
+        a.mass_amu = float(d["mass_amu"])
+        a.background_sigma = float(background_sigma)
+        a.cell_cm = float(cell_cm)
+        return a
+
+
+def _lam_arrays(lam_nm, tag):
+    lam = np.ascontiguousarray(np.asarray(lam_nm, dtype=np.float64))
+    tg = np.ascontiguousarray(np.asarray(tag, dtype=np.int32))
+    return lam, tg, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), tg.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def lte_populations(ctx: Context, atom: Atom, T, nh, out=None):
+    n = T.numel()
+    if out is None:
+        out = torch.empty((atom.n_level, n), dtype=torch.float64, device=T.device)
+    ctx._rc(lib().dex_lte_populations(ctx.handle, ctypes.byref(atom), n, _ptr(T), _ptr(nh), _ptr(out)))
+    return out
+
+
+def atom_eta_chi(ctx: Context, atom: Atom, lam_nm, tag, T, ne, pops, eta=None, chi=None):
+    n = T.numel()
+    lam, tg, lp, tp = _lam_arrays(lam_nm, tag)
+    if eta is None:
+        eta = torch.empty((lam.size, n), dtype=torch.float32, device=T.device)
+    if chi is None:
+        chi = torch.empty((lam.size, n), dtype=torch.float32, device=T.device)
+    ctx._rc(lib().dex_atom_eta_chi(ctx.handle, ctypes.byref(atom), n, lam.size, lp, tp, _ptr(T), _ptr(ne), _ptr(pops),
+                                   _ptr(eta), _ptr(chi)))
+    return eta, chi
+
+
+def rates_accumulate(ctx: Context, atom: Atom, lam_nm, tag, T, J, out=None):
+    n = T.numel()
+    lam, tg, lp, tp = _lam_arrays(lam_nm, tag)
+    if out is None:
+        out = torch.empty((max(atom.n_line, 1), n), dtype=torch.float64, device=T.device)
+    ctx._rc(lib().dex_rates_accumulate(ctx.handle, ctypes.byref(atom), n, lam.size, lp, tp, _ptr(T), _ptr(J),
+                                       _ptr(out)))
+    return out
+
+
+def se_solve(ctx: Context, atom: Atom, T, ne, nh, jbar, out=None):
+    n = T.numel()
+    if out is None:
+        out = torch.empty((atom.n_level, n), dtype=torch.float64, device=T.device)
+    ctx._rc(lib().dex_se_solve(ctx.handle, ctypes.byref(atom), n, _ptr(T), _ptr(ne), _ptr(nh), _ptr(jbar),
+                               _ptr(out)))
+    return out
+
+
+def lambda_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, nz: int, dirs, weights,
+                     n_iter: int, accelerated: bool = False, W: int = 8, max_mip: int = 3, iod: float = 1e-2,
+                     chi_ds_min: float = 0.25, band=None, pops=None):
+    """Fixed-length Lambda iteration: [eta, chi -> formal solution -> Jbar -> SE] x n_iter.
+
+    Every step is a library call; this function only sequences them.  The plain
+    variant solves at full resolution from every cell of every non-empty block
+    (``dex_formal_solve_dense`` over that probe list); the accelerated one builds
+    the MIP chains and runs the HDDA solve.  Returns the float64 populations.
+    """
+    n = nx * nz
+    L = int(np.asarray(lam_nm).size)
+    if pops is None:
+        pops = lte_populations(ctx, atom, T, nh)
+    eta = torch.empty((L, n), dtype=torch.float32, device=T.device)
+    chi = torch.empty_like(eta)
+    J = torch.empty_like(eta)
+    jbar = None
+    grid, mips, planes, probes = None, None, None, None
+    for _ in range(n_iter):
+        atom_eta_chi(ctx, atom, lam_nm, tag, T, ne, pops, eta, chi)
+        grid = grid_build(ctx, nx, nz, eta, chi, out=grid)
+        if accelerated:
+            mips = mips_build(ctx, grid, eta, chi, W, max_mip, iod, iod, chi_ds_min, out=mips)
+            formal_solve_hdda(ctx, grid, mips, dirs, weights, J=J, band=band)
+        else:
+            if probes is None:
+                off = grid.block_offset.view(grid.nbz, grid.nbx) >= 0
+                cell = off.repeat_interleave(BLOCK, 0).repeat_interleave(BLOCK, 1).reshape(-1)
+                probes = torch.nonzero(cell).to(torch.int32).reshape(-1)
+                Jp = torch.empty((L, probes.numel()), dtype=torch.float32, device=T.device)
+            planes = pack_planes(ctx, eta, chi, W, out=planes)
+            formal_solve_dense(ctx, nx, nz, L, W, planes, dirs, weights, probes=probes, J=Jp)
+            J.zero_()
+            J[:, probes.long()] = Jp
+        jbar = rates_accumulate(ctx, atom, lam_nm, tag, T, J, out=jbar)
+        pops = se_solve(ctx, atom, T, ne, nh, jbar, out=pops)
+    return pops

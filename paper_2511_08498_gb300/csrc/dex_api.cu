@@ -70,6 +70,64 @@ int fill_quadrature(dex_ctx* ctx, int n_dir, const float* dirs, const float* wei
     return DEX_OK;
 }
 
+constexpr double kH_ = 6.62607015e-27;
+constexpr double kC_ = 2.99792458e10;
+
+// Validate the atom and the wavelength samples; fill the launch parameters
+// (frequencies, per-line trapezoid weights in frequency, Einstein B).
+int fill_atom(dex_ctx* ctx, const dex_atom* atom, int n_lambda, const double* lambda_nm, const int* line_tag,
+              dex::AtomParams& P)
+{
+    if (!atom) return fail(ctx, DEX_ERR_ARG, "atom required");
+    if (atom->n_level < 2 || atom->n_level > DEX_MAX_LEVELS)
+        return fail(ctx, DEX_ERR_ARG, "n_level must be in [2, %d]", DEX_MAX_LEVELS);
+    if (atom->n_line < 0 || atom->n_line > DEX_MAX_LINES)
+        return fail(ctx, DEX_ERR_ARG, "n_line must be in [0, %d]", DEX_MAX_LINES);
+    for (int l = 0; l < atom->n_line; ++l) {
+        const int lo = atom->line_lower[l], up = atom->line_upper[l];
+        if (lo < 0 || up >= atom->n_level || lo >= up) return fail(ctx, DEX_ERR_ARG, "line %d has bad levels", l);
+        if (!(atom->line_A[l] > 0.0) || !(atom->line_lambda0_nm[l] > 0.0))
+            return fail(ctx, DEX_ERR_ARG, "line %d needs A > 0 and lambda0 > 0", l);
+    }
+    for (int i = 0; i < atom->n_level; ++i)
+        if (!(atom->g[i] > 0.0)) return fail(ctx, DEX_ERR_ARG, "statistical weight %d must be > 0", i);
+    if (!(atom->mass_amu > 0.0) || !(atom->cell_cm > 0.0) || !(atom->background_sigma >= 0.0))
+        return fail(ctx, DEX_ERR_ARG, "mass, cell size must be > 0 and background_sigma >= 0");
+    if (n_lambda < 0 || n_lambda > DEX_MAX_ATOM_LAMBDA)
+        return fail(ctx, DEX_ERR_ARG, "n_lambda must be in [0, %d]", DEX_MAX_ATOM_LAMBDA);
+    if (n_lambda > 0 && (!lambda_nm || !line_tag)) return fail(ctx, DEX_ERR_ARG, "lambda_nm and line_tag required");
+    P.atom = *atom;
+    P.n_lambda = n_lambda;
+    for (int k = 0; k < n_lambda; ++k) {
+        if (!(lambda_nm[k] > 0.0)) return fail(ctx, DEX_ERR_ARG, "wavelength %d must be > 0", k);
+        if (line_tag[k] < -1 || line_tag[k] >= atom->n_line) return fail(ctx, DEX_ERR_ARG, "bad line tag %d", k);
+        P.nu[k] = kC_ / (lambda_nm[k] * 1e-7);
+        P.tag[k] = (signed char)line_tag[k];
+        P.wq[k] = 0.0;
+    }
+    for (int l = 0; l < atom->n_line; ++l) {
+        P.nu0[l] = kC_ / (atom->line_lambda0_nm[l] * 1e-7);
+        P.b_ul[l] = atom->line_A[l] * kC_ * kC_ / (2.0 * kH_ * P.nu0[l] * P.nu0[l] * P.nu0[l]);
+        P.b_lu[l] = atom->g[atom->line_upper[l]] / atom->g[atom->line_lower[l]] * P.b_ul[l];
+        // trapezoid weights over the line's samples in increasing frequency
+        int idx[DEX_MAX_ATOM_LAMBDA], n = 0;
+        for (int k = 0; k < n_lambda; ++k)
+            if (line_tag[k] == l) idx[n++] = k;
+        for (int a = 1; a < n; ++a)  // insertion sort by frequency
+            for (int b = a; b > 0 && P.nu[idx[b]] < P.nu[idx[b - 1]]; --b) {
+                const int t = idx[b];
+                idx[b] = idx[b - 1];
+                idx[b - 1] = t;
+            }
+        for (int a = 0; a + 1 < n; ++a) {
+            const double h = P.nu[idx[a + 1]] - P.nu[idx[a]];
+            P.wq[idx[a]] += 0.5 * h;
+            P.wq[idx[a + 1]] += 0.5 * h;
+        }
+    }
+    return DEX_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -322,7 +380,8 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
 int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
                           const unsigned long long* state_words, const int* block_offset, const int* active,
                           const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
-                          float i_bc, float* J, float* I, unsigned long long* seg_count)
+                          int n_band, const float* band, float i_bc, float* J, float* I,
+                          unsigned long long* seg_count)
 {
     if (!ctx) return DEX_ERR_ARG;
     if (int r = check_sparse_grid(ctx, nx, nz)) return r;
@@ -333,6 +392,16 @@ int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int
     if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
     if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
     dex::HddaParams P{};
+    P.n_band = -1;
+    if (band != nullptr && n_band >= 0) {
+        if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);
+        for (int q = 0; q < n_band; ++q) {
+            if (std::isnan(band[q]) || (q > 0 && band[q] < band[q - 1]))
+                return fail(ctx, DEX_ERR_ARG, "distance thresholds must be non-decreasing numbers");
+            P.band[q] = band[q];
+        }
+        P.n_band = n_band;
+    }
     if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
     if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
         return fail(ctx, DEX_ERR_ARG, "null buffer");
@@ -365,6 +434,81 @@ int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int
     if (e == cudaSuccess) e = dex::launch_solve_hdda(ctx->stream, P);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_hdda launch");
     return ok(ctx);
+}
+
+int dex_lte_populations(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature, const float* nh,
+                        double* pops)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    dex::AtomParams* P = new (std::nothrow) dex::AtomParams();
+    if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    int r = fill_atom(ctx, atom, 0, nullptr, nullptr, *P);
+    if (!r && n_cells < 0) r = fail(ctx, DEX_ERR_ARG, "negative n_cells");
+    if (!r && n_cells > 0 && (!temperature || !nh || !pops)) r = fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!r) r = bind(ctx);
+    if (!r) {
+        cudaError_t e = dex::launch_lte_pops(ctx->stream, *P, n_cells, temperature, nh, pops);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "lte_pops launch") : ok(ctx);
+    }
+    delete P;
+    return r;
+}
+
+int dex_atom_eta_chi(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_lambda, const double* lambda_nm,
+                     const int* line_tag, const float* temperature, const float* ne, const double* pops, float* eta,
+                     float* chi)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    dex::AtomParams* P = new (std::nothrow) dex::AtomParams();
+    if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    int r = fill_atom(ctx, atom, n_lambda, lambda_nm, line_tag, *P);
+    if (!r && n_cells < 0) r = fail(ctx, DEX_ERR_ARG, "negative n_cells");
+    if (!r && n_cells > 0 && n_lambda > 0 && (!temperature || !ne || !pops || !eta || !chi))
+        r = fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!r) r = bind(ctx);
+    if (!r) {
+        cudaError_t e = dex::launch_atom_eta_chi(ctx->stream, *P, n_cells, temperature, ne, pops, eta, chi);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "atom_eta_chi launch") : ok(ctx);
+    }
+    delete P;
+    return r;
+}
+
+int dex_rates_accumulate(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_lambda, const double* lambda_nm,
+                         const int* line_tag, const float* temperature, const float* J, double* jbar)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    dex::AtomParams* P = new (std::nothrow) dex::AtomParams();
+    if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    int r = fill_atom(ctx, atom, n_lambda, lambda_nm, line_tag, *P);
+    if (!r && n_cells < 0) r = fail(ctx, DEX_ERR_ARG, "negative n_cells");
+    if (!r && n_cells > 0 && (!temperature || !J || !jbar)) r = fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!r) r = bind(ctx);
+    if (!r) {
+        cudaError_t e = dex::launch_rates(ctx->stream, *P, n_cells, temperature, J, jbar);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "rates launch") : ok(ctx);
+    }
+    delete P;
+    return r;
+}
+
+int dex_se_solve(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature, const float* ne,
+                 const float* nh, const double* jbar, double* pops)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    dex::AtomParams* P = new (std::nothrow) dex::AtomParams();
+    if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    int r = fill_atom(ctx, atom, 0, nullptr, nullptr, *P);
+    if (!r && n_cells < 0) r = fail(ctx, DEX_ERR_ARG, "negative n_cells");
+    if (!r && n_cells > 0 && (!temperature || !ne || !nh || !pops || (atom->n_line > 0 && !jbar)))
+        r = fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!r) r = bind(ctx);
+    if (!r) {
+        cudaError_t e = dex::launch_se_solve(ctx->stream, *P, n_cells, temperature, ne, nh, jbar, pops);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "se_solve launch") : ok(ctx);
+    }
+    delete P;
+    return r;
 }
 
 }  // extern "C"

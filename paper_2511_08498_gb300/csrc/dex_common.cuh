@@ -42,11 +42,33 @@ constexpr float kG5 = (float)taylor_coef(5);
 constexpr float kSeriesCut = -0.14426950f;
 constexpr float kNegLog2e = -1.4426950408889634f;
 
+// Transparent emitters (chi = 0, eta > 0) are stored as chi = eta * 2^-60 and
+// S = 2^60, so that S (1 - e^{-chi len}) = eta len (1 - O(eta len 2^-60)) with no
+// per-wavelength branch in the solvers.  Exact to float32 for eta <= 2^36.
+constexpr float kEmitterScale = 1.152921504606846976e18f;     // 2^60
+constexpr float kEmitterInvScale = 8.673617379884035e-19f;    // 2^-60
+constexpr float kEmitterMaxEta = 68719476736.0f;              // 2^36
+
+// Record entry (S, chi) of a voxel with emissivity e and opacity c (both >= 0).
+__host__ __device__ __forceinline__ void encode_voxel(float e, float c, float& S, float& chi)
+{
+    if (c > 0.0f) {
+        S = e / c;
+        chi = c;
+    } else if (e > 0.0f) {
+        S = kEmitterScale;
+        chi = e * kEmitterInvScale;
+    } else {
+        S = 0.0f;
+        chi = 0.0f;
+    }
+}
+
 // One voxel segment of length `len` for one wavelength: the piecewise-constant
 // solution of Eq. RteIntegral composited front to back (probe outward):
 //   I += T * S * (1 - e^{-chi len});  T *= e^{-chi len}
-// With chi == 0 the planes store S = eta and the contribution is eta * len.
-__device__ __forceinline__ void segment(float S, float chi, float nl2, float len, float& I, float& T)
+// nl2 = -len log2(e) is shared by the wavelengths of a record.
+__device__ __forceinline__ void segment(float S, float chi, float nl2, float& I, float& T)
 {
     const float x = chi * nl2;             // -tau log2(e)
     const float e = ex2_approx(x);         // e^{-tau}
@@ -55,8 +77,7 @@ __device__ __forceinline__ void segment(float S, float chi, float nl2, float len
     p = fmaf(x, p, kG2);
     p = fmaf(x, p, kG1);
     const float g = (x > kSeriesCut) ? x * p : 1.0f - e;  // 1 - e^{-tau}
-    const float src = (chi > 0.0f) ? S * g : S * len;
-    I = fmaf(T, src, I);
+    I = fmaf(T, S * g, I);
     T *= e;
 }
 

@@ -38,6 +38,8 @@ struct MipParams {
 
 struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active;
+    int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
+    float band[4];
     long long n_cells;
     const float* bricks;
     const unsigned long long* words;
@@ -51,6 +53,26 @@ struct HddaParams {
     unsigned int* status;
     Quadrature quad;
 };
+
+struct AtomParams {
+    dex_atom atom;
+    int n_lambda;
+    double nu[DEX_MAX_ATOM_LAMBDA];    // sample frequencies (Hz)
+    double wq[DEX_MAX_ATOM_LAMBDA];    // trapezoid weight in frequency within the sample's line
+    signed char tag[DEX_MAX_ATOM_LAMBDA];
+    double nu0[DEX_MAX_LINES];
+    double b_ul[DEX_MAX_LINES];
+    double b_lu[DEX_MAX_LINES];
+};
+
+cudaError_t launch_lte_pops(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T,
+                            const float* nh, double* pops);
+cudaError_t launch_atom_eta_chi(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T,
+                                const float* ne, const double* pops, float* eta, float* chi);
+cudaError_t launch_rates(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T, const float* J,
+                         double* jbar);
+cudaError_t launch_se_solve(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T, const float* ne,
+                            const float* nh, const double* jbar, double* pops);
 
 int chain_length(int max_mip);
 cudaError_t launch_synth_static_line(cudaStream_t s, long long n_cells, int n_lambda, const float* chi_c,

@@ -8,14 +8,12 @@
 // match.  Wavelength batch is the slowest grid dimension so that one batch
 // (nx * nz * 8W bytes) is the L2-resident working set at a time.
 //
-// Plane crossings are evaluated from the integer voxel offset,
-//   t_next = (offset + 1/2) / d,
-// instead of being accumulated (t += 1/d): every t is then within one rounding
-// of exact, and the boundary plane's t is bit-identical to the exit parameter,
-// so a ray can never step outside the grid.
+// Plane crossings are evaluated from exact half-integer plane offsets,
+//   t_next = offset * fl(1/d)  (+ a low-order part, see AxisParam),
+// instead of being accumulated (t += 1/d): every t is within one rounding of
+// exact, and the boundary plane's t is bit-identical to the exit parameter, so
+// a ray never steps outside the grid.
 #include "dex_internal.h"
-
-#include <cfloat>
 
 namespace dex {
 
@@ -37,13 +35,12 @@ __global__ void k_pack_planes(long long n_cells, int n_lambda, int W, int n_batc
             float S = 0.0f, x = 0.0f;
             if (l < n_lambda) {
                 const float e = eta[(long long)l * n_cells + c];
-                x = chi[(long long)l * n_cells + c];
-                if (!(x >= 0.0f) || !(e >= 0.0f) || !isfinite(x) || !isfinite(e)) {
+                const float k = chi[(long long)l * n_cells + c];
+                if (!(k >= 0.0f) || !(e >= 0.0f) || !isfinite(k) || !isfinite(e) ||
+                    (k == 0.0f && e > kEmitterMaxEta)) {
                     bad = true;
-                    x = 0.0f;
-                    S = 0.0f;
                 } else {
-                    S = (x > 0.0f) ? e / x : e;
+                    encode_voxel(e, k, S, x);
                 }
             }
             rec[w] = S;
@@ -53,7 +50,7 @@ __global__ void k_pack_planes(long long n_cells, int n_lambda, int W, int n_batc
     }
 }
 
-template <int W>
+template <int W, bool COUNT>
 __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
 {
     const int b = blockIdx.y;
@@ -78,7 +75,10 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
         j = c / P.nx;
     }
 
-    const float* __restrict__ base = P.planes + (size_t)b * P.n_cells * (2 * W);
+    constexpr int REC = 2 * W;
+    const float* __restrict__ base = P.planes + (size_t)b * P.n_cells * REC;
+    const float* __restrict__ origin_rec = base + ((size_t)j * P.nx + i) * REC;
+    const long long row = (long long)P.nx * REC;
     const int cap = P.nx + P.nz + 4;
     float Jw[W];
 #pragma unroll
@@ -90,40 +90,43 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
         const float dx = P.quad.dx[k], dz = P.quad.dz[k];
         // a zero component counts as positive, so its plane offsets are positive
         // and their parameters (offset * inf) are +inf: that axis never steps
-        const int sx = dx < 0.0f ? -1 : 1, sz = dz < 0.0f ? -1 : 1;
+        const bool negx = dx < 0.0f, negz = dz < 0.0f;
+        const int sx = negx ? -1 : 1, sz = negz ? -1 : 1;
+        const float fsx = (float)sx, fsz = (float)sz;
+        const long long stepx = negx ? -REC : REC, stepz = negz ? -row : row;
         const AxisParam ax = axis_param(dx), az = axis_param(dz);
         // plane offsets from the origin (half-integers, exact): next plane, exit plane
-        float Px = dx < 0.0f ? -0.5f : 0.5f, Pz = dz < 0.0f ? -0.5f : 0.5f;
-        const float Ex = dx < 0.0f ? (float)(-i) - 0.5f : (float)(P.nx - i) - 0.5f;
-        const float Ez = dz < 0.0f ? (float)(-j) - 0.5f : (float)(P.nz - j) - 0.5f;
+        float Px = negx ? -0.5f : 0.5f, Pz = negz ? -0.5f : 0.5f;
+        const float Ex = negx ? (float)(-i) - 0.5f : (float)(P.nx - i) - 0.5f;
+        const float Ez = negz ? (float)(-j) - 0.5f : (float)(P.nz - j) - 0.5f;
         const float t2 = fminf(Ex * ax.ih, Ez * az.ih);
 
-        int di = 0, dj = 0;
+        int ci = i, cj = j;
+        const float* rp = origin_rec;
         float th_prev = 0.0f, tl_prev = 0.0f;
         float I[W], T[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
-
         for (int it = 0;; ++it) {
             const float tnx = Px * ax.ih, tnz = Pz * az.ih;
             const bool on_x = tnx <= tnz;
             const float th = on_x ? tnx : tnz;
             const float tl = plane_lo(on_x ? Px : Pz, on_x ? ax : az, th);
-            const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
-            const int ci = i + di, cj = j + dj;
+            const float len = (th - th_prev) + (tl - tl_prev);
             if (it >= cap || (unsigned)ci >= (unsigned)P.nx || (unsigned)cj >= (unsigned)P.nz) {
                 capped = true;
                 break;
             }
-            const Record<W> r = load_record<W>(base + ((size_t)cj * P.nx + ci) * (2 * W));
+            const Record<W> r = load_record<W>(rp);
             const float nl2 = len * kNegLog2e;
 #pragma unroll
-            for (int w = 0; w < W; ++w) segment(r.S[w], r.chi[w], nl2, len, I[w], T[w]);
-            nseg += (th > th_prev);
+            for (int w = 0; w < W; ++w) segment(r.S[w], r.chi[w], nl2, I[w], T[w]);
+            if (COUNT) nseg += (th > th_prev);
+            if (th >= t2) break;
             th_prev = th;
             tl_prev = tl;
-            if (th >= t2) break;
-            if (on_x) { di += sx; Px += (float)sx; } else { dj += sz; Pz += (float)sz; }
+            if (on_x) { Px += fsx; ci += sx; rp += stepx; }
+            else { Pz += fsz; cj += sz; rp += stepz; }
         }
         const float wk = P.quad.w[k];
 #pragma unroll
@@ -141,7 +144,14 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
         if (l < P.n_lambda) P.J[(size_t)l * P.n_probe + p] = Jw[w];
     }
     if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
-    if (P.seg_count != nullptr) atomicAdd(P.seg_count, (unsigned long long)nseg);
+    if (COUNT && P.seg_count != nullptr) atomicAdd(P.seg_count, (unsigned long long)nseg);
+}
+
+template <int W>
+void launch_dense_w(dim3 grid, cudaStream_t s, const DenseParams& P)
+{
+    if (P.seg_count) k_solve_dense<W, true><<<grid, 256, 0, s>>>(P);
+    else k_solve_dense<W, false><<<grid, 256, 0, s>>>(P);
 }
 
 }  // namespace
@@ -169,10 +179,10 @@ cudaError_t launch_solve_dense(cudaStream_t s, const DenseParams& P)
         grid = dim3((unsigned)((P.n_probe + 255) / 256), (unsigned)P.n_batch);
     }
     switch (P.W) {
-        case 1: k_solve_dense<1><<<grid, 256, 0, s>>>(P); break;
-        case 2: k_solve_dense<2><<<grid, 256, 0, s>>>(P); break;
-        case 4: k_solve_dense<4><<<grid, 256, 0, s>>>(P); break;
-        case 8: k_solve_dense<8><<<grid, 256, 0, s>>>(P); break;
+        case 1: launch_dense_w<1>(grid, s, P); break;
+        case 2: launch_dense_w<2>(grid, s, P); break;
+        case 4: launch_dense_w<4>(grid, s, P); break;
+        case 8: launch_dense_w<8>(grid, s, P); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

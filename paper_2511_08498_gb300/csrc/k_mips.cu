@@ -60,10 +60,7 @@ __device__ __forceinline__ void store_record(float* rec, const float* e, const f
 {
     float v[2 * W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) {
-        v[w] = c[w] > 0.0f ? e[w] / c[w] : e[w];
-        v[W + w] = c[w];
-    }
+    for (int w = 0; w < W; ++w) encode_voxel(e[w], c[w], v[w], v[W + w]);
     if constexpr (W >= 2) {
         float4* q = reinterpret_cast<float4*>(rec);
 #pragma unroll
@@ -101,7 +98,8 @@ __global__ void __launch_bounds__(256) k_mips_build(const MipParams P)
             if (l < P.n_lambda) {
                 ev = P.eta[l * n_cells + c];
                 cv = P.chi[l * n_cells + c];
-                if (!(ev >= 0.0f) || !(cv >= 0.0f) || !isfinite(ev) || !isfinite(cv)) {
+                if (!(ev >= 0.0f) || !(cv >= 0.0f) || !isfinite(ev) || !isfinite(cv) ||
+                    (cv == 0.0f && ev > kEmitterMaxEta)) {
                     bad = true;
                     ev = cv = 0.0f;
                 }

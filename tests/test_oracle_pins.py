@@ -350,3 +350,53 @@ def test_generators_are_deterministic():
     assert abs(c["empty_block_frac"] - 0.4) < 0.04
     # top 30% of the dense model is transparent and the rest is not
     assert (a["chi"][0, 32 - 9:] == 0).all() and (a["chi"][0, :32 - 9] > 0).all()
+
+
+# ------------------------------------------- distance-limited MIP levels ----
+
+def _two_block_model():
+    # 32 x 16 grid: block A (x < 16) and block B (x >= 16), both selectable at level 1,
+    # with a strongly varying B so that levels 0 and 1 give different intensities
+    rng = np.random.default_rng(11)
+    chi = rng.uniform(0.05, 0.6, (1, 16, 32))
+    eta = chi * rng.uniform(0.5, 2.0, (1, 16, 32))
+    levels, _ = mips.mip_chain(eta, chi, 1, 1e9, 1e9, 0.0)
+    lev = np.ones((1, 1, 2), dtype=np.int32)
+    return eta, chi, levels, lev
+
+
+def test_banded_levels_reduce_to_plain_and_to_expanded():
+    eta, chi, levels, lev = _two_block_model()
+    dirs, w = synth.directions(8)
+    probes = np.arange(32 * 16, dtype=np.int32)
+    # no level above 0 allowed anywhere: the plain solution
+    J0 = lc.formal_solve_banded(levels, lev, 16, 1, [1e9], dirs, w, probes)
+    np.testing.assert_allclose(J0, lc.formal_solve(eta, chi, dirs, w, probes=probes), rtol=1e-13)
+    # every level allowed from t = 0: the expanded-grid solution
+    J1 = lc.formal_solve_banded(levels, lev, 16, 1, [0.0], dirs, w, probes)
+    e2, c2 = mips.expand(levels, lev, 1)
+    np.testing.assert_allclose(J1, lc.formal_solve(e2, c2, dirs, w, probes=probes), rtol=1e-13)
+    assert np.abs(J1 - J0).max() > 1e-3  # the two limits differ for this model
+
+
+def test_banded_level_switches_at_block_entry_distance():
+    # A +x ray from cell (i, 3) enters block B at t = 15.5 - i.  With threshold 10,
+    # probes with i <= 5 see B at level 1, probes with i >= 6 at level 0; block A
+    # (entered at t = 0) is always at level 0.  Build the expected intensity by hand
+    # from per-cell values of the chosen level.
+    eta, chi, levels, lev = _two_block_model()
+    e1 = np.repeat(np.repeat(levels[1][0][0], 2, 0), 2, 1)
+    c1 = np.repeat(np.repeat(levels[1][1][0], 2, 0), 2, 1)
+    for i in (2, 5, 6, 12):
+        p = 3 * 32 + i
+        _, I = lc.formal_solve_banded(levels, lev, 16, 1, [10.0], [[1.0, 0.0]], [1.0],
+                                      np.array([p], np.int32), want_intensity=True)
+        use1 = (15.5 - i) >= 10.0
+        e_row = np.concatenate([eta[0, 3, :16], (e1 if use1 else eta[0])[3, 16:]])
+        c_row = np.concatenate([chi[0, 3, :16], (c1 if use1 else chi[0])[3, 16:]])
+        ref = 0.0
+        for x in range(31, i - 1, -1):  # upwind from the boundary to the probe
+            L = 0.5 if x == i else 1.0
+            tau = c_row[x] * L
+            ref = ref * math.exp(-tau) + e_row[x] / c_row[x] * (1 - math.exp(-tau))
+        assert abs(I[0, 0, 0] - ref) < 1e-12 * ref

@@ -281,3 +281,28 @@ def test_axis_parallel_rays_through_levels(ctx):
     robust = robust_level_mask(o["stats"], o["lev"], 8, 16, 3, 1.0, 1.0, 0.25)
     assert robust.all()
     assert_rel(I.cpu().numpy()[:, :, o["probes"]], o["I"], what="axis-parallel")
+
+
+@pytest.mark.parametrize("band", [[5.3, 21.7, 60.1], [0.0], [], [2.2, 2.2, 9.9]])
+def test_distance_limited_levels_match_oracle(ctx, band):
+    """Section 4.1's near-field-at-full-resolution limit, long-characteristics form:
+    a block first entered at ray parameter t uses at most the number of thresholds <= t."""
+    from paper_2511_08498_gb300 import api
+    nx, nz, L, W = 128, 96, 16, 8
+    m = line_model(nx, nz, L, synth.SEED_BASE + 470)
+    eg, cg = gpu_line_eta_chi(ctx, m)
+    er, cr = oracle_line_eta_chi(m)
+    dirs, w = synth.directions(16)
+    te = 1.0
+    grid = api.grid_build(ctx, nx, nz, eg, cg)
+    mp = api.mips_build(ctx, grid, eg, cg, W, 3, te, te, 0.25, log_mean=False)
+    J, I, _ = api.formal_solve_hdda(ctx, grid, mp, dirs, w, want_intensity=True, band=band)
+    ctx.check()
+    levels, passes, st = omips.mip_chain(er, cr, 3, te, te, 0.25, mean="linear", stats=True)
+    empty = omips.block_empty(er, cr, 16)
+    lev = omips.block_levels(passes, empty, 16, W)
+    assert robust_level_mask(st, lev, W, 16, 3, te, te, 0.25).all()
+    probes = omips.probes_of_blocks(empty, 16)
+    Jr, Ir = lc.formal_solve_banded(levels, lev, 16, W, band, dirs, w, probes, want_intensity=True)
+    assert_rel(I.cpu().numpy()[:, :, probes], Ir, what=f"I band={band}")
+    assert_rel(J.cpu().numpy()[:, probes], Jr, what=f"J band={band}")
