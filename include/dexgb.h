@@ -288,6 +288,73 @@ int dex_rates_accumulate(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_
 int dex_se_solve(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature, const float* ne,
                  const float* nh, const double* jbar, double* pops);
 
+/* ------------------------------------------------------------------ Voigt --
+ *
+ * Section 3.2: the Voigt function H(a, x) = Re w(x + i a) by HUM1WEI24
+ * (Humlicek 1982 region I for |x| + a >= 15, Weideman 1994 with 24 terms
+ * otherwise), float32; the form the Core-and-Voigt solver evaluates per segment.
+ * a, x, h: device [n] (a >= 0).
+ */
+int dex_voigt(dex_ctx* ctx, int n, const float* a, const float* x, float* h);
+
+/* ------------------------------------------------------ Core and Voigt --
+ *
+ * Section 3.2: a moving medium with one spectral line over an isotropic
+ * background.  Per cell (device [nz][nx] float32 fields): line strengths eta*,
+ * chi* (per km/s), Voigt damping a, thermal width v_th (km/s), velocity v_x, v_z
+ * (km/s), background eta_c, chi_c.  Wavelengths are velocity offsets dv (km/s)
+ * from the rest wavelength; c_kms is the speed of light in km/s.  For a ray
+ * traced toward +d the radiation propagates along w = -d and
+ *   u = dv + v.w,  s = 1/(1 + dv/c),  phi = H(a/s^2, u/v_th)/(sqrt(pi) v_th),
+ *   eta = eta* s phi + eta_c,  chi = chi* s phi + chi_c,
+ * with H by HUM1WEI24 (dex_voigt).  n_lambda <= DEX_MAX_CAV_LAMBDA.
+ */
+#define DEX_MAX_CAV_LAMBDA 256
+
+typedef struct {
+    const float* eta_star;
+    const float* chi_star;
+    const float* damping;
+    const float* vth;
+    const float* vx;
+    const float* vz;
+    const float* eta_c;
+    const float* chi_c;
+} dex_cav_fields;
+
+/* Sparsity map + Morton layout from the CaV fields (block empty when eta*, chi*,
+ * eta_c, chi_c all vanish in it); outputs as dex_grid_build. */
+int dex_cav_grid_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int* block_offset, int* active,
+                       int* n_active);
+
+/* Floats of the CaV parameter bricks: capacity * dex_chain_voxels(max_mip) * 8. */
+size_t dex_cav_brick_floats(int capacity, int max_mip);
+
+/*
+ * Box-filter MIP chains of the 8 voxel parameters (one set for all wavelengths:
+ * bricks [capacity][chain][8] = eta*, chi*, a, 1/v_th, v_x, v_z, eta_c, chi_c) and
+ * the block level per wavelength batch: Eq. IoD of ln(eta Ds), ln(chi Ds) with each
+ * child's eta, chi evaluated at the Doppler shift closest to line centre its speed
+ * allows (|u| = max(0, |dv| - |v|), Section 3.2), plus the always-average rule.
+ * dv: host [n_lambda].  Other arguments as dex_mips_build (log_mean is ignored).
+ */
+int dex_cav_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int n_lambda, int W,
+                       const float* dv, float c_kms, const int* active, const int* n_active, int capacity,
+                       const dex_vlm_params* params, const signed char* level_cap, float* bricks,
+                       unsigned long long* state_words);
+
+/*
+ * CaV formal solution: the hierarchical DDA of dex_formal_solve_hdda over the
+ * parameter bricks, evaluating eta, chi per segment and wavelength for the ray's
+ * direction (HUM1WEI24 Voigt profile).  Arguments as dex_formal_solve_hdda plus
+ * dv (host [n_lambda]) and c_kms.
+ */
+int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv,
+                         float c_kms, const float* bricks, const unsigned long long* state_words,
+                         const int* block_offset, const int* active, const int* n_active, int capacity, int n_dir,
+                         const float* dirs, const float* weights, int n_band, const float* band, float i_bc,
+                         float* J, float* I, unsigned long long* seg_count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,13 +4,19 @@ TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU-baseline leg).
 
 * ``exact``: the Faddeeva function from scipy (``scipy.special.wofz``): the judge.
 * ``hum1wei24``: the approximation Section 3.2 names (Schreier 2018, "HUM1WEI24"),
-  restated from its published sources, in float64:
+  restated from its published sources, in float64 (``method="hum1wei24"``):
     - |x| + y >= 15: region I of Humlicek (1982), w(z) = i z / (sqrt(pi) (z^2 - 1/2));
     - otherwise Weideman (1994) with N = 24 terms:
         w(z) = 2 p(Z) / (L - i z)^2 + 1 / (sqrt(pi) (L - i z)),
         Z = (L + i z) / (L - i z),  p(Z) = sum_{n=1..N} a_n Z^(n-1),  L = sqrt(N / sqrt 2),
       where a_n are the Fourier coefficients of f(theta) = exp(-t^2) (L^2 + t^2),
       t = L tan(theta / 2), by the trapezoid rule on 2M = 4N points (f(-pi) = 0).
+* ``hum1wei24_cf``: the form the GPU evaluates: the same, except that for
+  5 <= |x| + y < 15 the Weideman sum is replaced by the 8-term Laplace continued
+  fraction w(z) = (i / sqrt(pi)) / (z - (1/2) / (z - 1 / (z - (3/2) / ...)))
+  (Gautschi 1970), evaluated from the innermost term.  In float32 the Weideman
+  sum cancels O(1) terms down to H ~ 1e-5 in the line wings; the continued
+  fraction does not.
 """
 
 from __future__ import annotations
@@ -57,10 +63,34 @@ def hum1wei24(x, y):
     return out
 
 
+def laplace_cf(x, y, n_terms: int = 8):
+    """w(x + i y) from the Laplace continued fraction with ``n_terms`` levels."""
+    z = np.asarray(x, dtype=np.float64) + 1j * np.asarray(y, dtype=np.float64)
+    f = z.copy()
+    for k in range(n_terms, 0, -1):
+        f = z - (k / 2.0) / f
+    return 1j / (np.sqrt(np.pi) * f)
+
+
+def hum1wei24_cf(x, y):
+    """w(x + i y): Humlicek region I for s >= 15, continued fraction for 5 <= s < 15,
+    Weideman-24 for s < 5 (s = |x| + y)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    x, y = np.broadcast_arrays(x, y)
+    out = hum1wei24(x, y)
+    s = np.abs(x) + y
+    band = (s >= 5.0) & (s < 15.0)
+    out[band] = laplace_cf(x[band], y[band])
+    return out
+
+
 def voigt_h(a, x, method: str = "exact"):
     """H(a, x) = Re w(x + i a) (a >= 0)."""
     if method == "exact":
         return np.real(wofz(np.asarray(x, dtype=np.float64) + 1j * np.asarray(a, dtype=np.float64)))
     if method == "hum1wei24":
         return np.real(hum1wei24(x, a))
+    if method == "hum1wei24_cf":
+        return np.real(hum1wei24_cf(x, a))
     raise ValueError(method)

@@ -47,6 +47,14 @@ PROTOTYPES = {
     "dex_rates_accumulate": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p]),
     "dex_se_solve": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 5),
+    "dex_voigt": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
+    "dex_cav_grid_build": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dex_cav_brick_floats": (c_size_t, [c_int, c_int]),
+    "dex_cav_mips_build": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_fp, c_float, c_void_p, c_void_p,
+                                   c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dex_formal_solve_cav": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_fp, c_float, c_void_p, c_void_p,
+                                     c_void_p, c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float,
+                                     c_void_p, c_void_p, c_void_p]),
 }
 
 

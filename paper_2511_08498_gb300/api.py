@@ -367,3 +367,87 @@ def lambda_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, 
         jbar = rates_accumulate(ctx, atom, lam_nm, tag, T, J, out=jbar)
         pops = se_solve(ctx, atom, T, ne, nh, jbar, out=pops)
     return pops
+
+
+def voigt(ctx: Context, a: torch.Tensor, x: torch.Tensor, out=None):
+    """H(a, x) by HUM1WEI24 (``dex_voigt``); a, x float32 CUDA tensors of equal size."""
+    if out is None:
+        out = torch.empty_like(x)
+    ctx._rc(lib().dex_voigt(ctx.handle, x.numel(), _ptr(a), _ptr(x), _ptr(out)))
+    return out
+
+
+# --------------------------------------------------------- Core and Voigt --
+
+CAV_FIELDS = ("eta_star", "chi_star", "damping", "vth", "vx", "vz", "eta_c", "chi_c")
+
+
+class CavFields(ctypes.Structure):
+    """``dex_cav_fields``: device pointers of the 8 per-cell CaV fields."""
+    _fields_ = [(k, ctypes.c_void_p) for k in CAV_FIELDS]
+
+    @classmethod
+    def from_tensors(cls, t: dict):
+        return cls(*[t[k].data_ptr() for k in CAV_FIELDS])
+
+
+class CavMips:
+    def __init__(self, bricks, words, W, max_mip, dv, c_kms, capacity):
+        self.bricks, self.words, self.W, self.max_mip = bricks, words, W, max_mip
+        self.dv = np.ascontiguousarray(np.asarray(dv, dtype=np.float32))
+        self.c_kms, self.capacity = float(c_kms), capacity
+        self.n_lambda = self.dv.size
+
+
+def cav_grid_build(ctx: Context, nx: int, nz: int, fields: dict, out: SparseGrid | None = None):
+    nb = (nx // BLOCK) * (nz // BLOCK)
+    dev = fields["chi_c"].device
+    if out is None:
+        out = SparseGrid(nx, nz, torch.empty(nb, dtype=torch.int32, device=dev),
+                         torch.zeros(nb, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.int32, device=dev))
+    f = CavFields.from_tensors(fields)
+    ctx._rc(lib().dex_cav_grid_build(ctx.handle, nx, nz, ctypes.byref(f), _ptr(out.block_offset), _ptr(out.active),
+                                     _ptr(out.n_active_dev)))
+    return out
+
+
+def cav_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: float, W: int, max_mip: int,
+                   iod_eta: float, iod_chi: float, chi_ds_min: float = 0.25, level_cap=None, capacity=None,
+                   out: CavMips | None = None):
+    cap = grid.n_blocks if capacity is None else int(capacity)
+    dvh = np.ascontiguousarray(np.asarray(dv, dtype=np.float32))
+    n_batch = -(-dvh.size // W)
+    dev = fields["chi_c"].device
+    if out is None:
+        nf = int(lib().dex_cav_brick_floats(cap, max_mip))
+        out = CavMips(torch.empty(max(nf, 4), dtype=torch.float32, device=dev),
+                      torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=dev),
+                      W, max_mip, dvh, c_kms, cap)
+    f = CavFields.from_tensors(fields)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0)
+    fp = ctypes.POINTER(ctypes.c_float)
+    ctx._rc(lib().dex_cav_mips_build(ctx.handle, grid.nx, grid.nz, ctypes.byref(f), dvh.size, W,
+                                     dvh.ctypes.data_as(fp), float(c_kms), _ptr(grid.active), _ptr(grid.n_active_dev),
+                                     cap, ctypes.byref(p), _ptr(level_cap), _ptr(out.bricks), _ptr(out.words)))
+    return out
+
+
+def formal_solve_cav(ctx: Context, grid: SparseGrid, mips: CavMips, dirs, weights, band=None, i_bc: float = 0.0,
+                     want_intensity: bool = False, count_segments: bool = False, J: torch.Tensor | None = None):
+    """Core-and-Voigt solve (``dex_formal_solve_cav``); outputs as :func:`formal_solve_hdda`."""
+    d, w = _quadrature(dirs, weights)
+    dev = mips.bricks.device
+    n_cells = grid.nx * grid.nz
+    L = mips.n_lambda
+    if J is None:
+        J = torch.empty((L, n_cells), dtype=torch.float32, device=dev)
+    I = torch.empty((L, d.shape[0], n_cells), dtype=torch.float32, device=dev) if want_intensity else None
+    seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
+    fp = ctypes.POINTER(ctypes.c_float)
+    b = None if band is None else _host_f32(band).reshape(-1)
+    ctx._rc(lib().dex_formal_solve_cav(
+        ctx.handle, grid.nx, grid.nz, L, mips.W, mips.max_mip, mips.dv.ctypes.data_as(fp), mips.c_kms,
+        _ptr(mips.bricks), _ptr(mips.words), _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev),
+        mips.capacity, d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
+        None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+    return J, I, seg

@@ -511,4 +511,173 @@ int dex_se_solve(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* t
     return r;
 }
 
+int dex_voigt(dex_ctx* ctx, int n, const float* a, const float* x, float* h)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (n < 0) return fail(ctx, DEX_ERR_ARG, "negative n");
+    if (n == 0) return ok(ctx);
+    if (!a || !x || !h) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_voigt(ctx->stream, n, a, x, h);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "voigt launch");
+    return ok(ctx);
+}
+
+static int cav_fields(dex_ctx* ctx, const dex_cav_fields* f, dex::CavFields& F)
+{
+    if (!f) return fail(ctx, DEX_ERR_ARG, "fields required");
+    if (!f->eta_star || !f->chi_star || !f->damping || !f->vth || !f->vx || !f->vz || !f->eta_c || !f->chi_c)
+        return fail(ctx, DEX_ERR_ARG, "every CaV field pointer is required");
+    F = dex::CavFields{f->eta_star, f->chi_star, f->damping, f->vth, f->vx, f->vz, f->eta_c, f->chi_c};
+    return DEX_OK;
+}
+
+static int cav_lambda(dex_ctx* ctx, int n_lambda, const float* dv, float c_kms)
+{
+    if (n_lambda < 1 || n_lambda > DEX_MAX_CAV_LAMBDA)
+        return fail(ctx, DEX_ERR_ARG, "n_lambda must be in [1, %d]", DEX_MAX_CAV_LAMBDA);
+    if (!dv) return fail(ctx, DEX_ERR_ARG, "dv (host) required");
+    if (!(c_kms > 0.0f) || !std::isfinite(c_kms)) return fail(ctx, DEX_ERR_ARG, "c_kms must be > 0");
+    for (int l = 0; l < n_lambda; ++l)
+        if (!std::isfinite(dv[l]) || !(1.0f + dv[l] / c_kms > 0.0f)) return fail(ctx, DEX_ERR_ARG, "bad dv[%d]", l);
+    return DEX_OK;
+}
+
+int dex_cav_grid_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int* block_offset, int* active,
+                       int* n_active)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_sparse_grid(ctx, nx, nz)) return r;
+    dex::CavFields F;
+    if (int r = cav_fields(ctx, fields, F)) return r;
+    if (!block_offset || !active || !n_active) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_cav_grid_build(ctx->stream, nx, nz, F, block_offset, active, n_active);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cav_grid_build launch");
+    return ok(ctx);
+}
+
+size_t dex_cav_brick_floats(int capacity, int max_mip)
+{
+    if (capacity < 0 || max_mip < 0 || max_mip > 4) return 0;
+    return (size_t)capacity * (size_t)dex::chain_length(max_mip) * 8;
+}
+
+int dex_cav_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int n_lambda, int W,
+                       const float* dv, float c_kms, const int* active, const int* n_active, int capacity,
+                       const dex_vlm_params* params, const signed char* level_cap, float* bricks,
+                       unsigned long long* state_words)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_sparse_grid(ctx, nx, nz)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (int r = cav_lambda(ctx, n_lambda, dv, c_kms)) return r;
+    dex::CavMipParams P{};
+    if (int r = cav_fields(ctx, fields, P.F)) return r;
+    if (!params) return fail(ctx, DEX_ERR_ARG, "params required");
+    if (params->max_mip < 0 || params->max_mip > 4) return fail(ctx, DEX_ERR_ARG, "max_mip must be in [0, 4]");
+    if (std::isnan(params->iod_eta) || std::isnan(params->iod_chi) || std::isnan(params->chi_ds_min))
+        return fail(ctx, DEX_ERR_ARG, "NaN threshold");
+    const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
+    if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
+    if (!active || !n_active || !bricks || !state_words) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(bricks, 16)) return fail(ctx, DEX_ERR_ARG, "bricks must be 16-byte aligned");
+    P.nx = nx;
+    P.nz = nz;
+    P.nbx = nx / DEX_BLOCK;
+    P.nbz = nz / DEX_BLOCK;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.max_mip = params->max_mip;
+    P.chain = dex::chain_length(params->max_mip);
+    P.n_words = (int)dex_state_words(nx, nz);
+    P.cap_active = capacity;
+    P.thr_eta = params->iod_eta;
+    P.thr_chi = params->iod_chi;
+    P.chi_ds_min = params->chi_ds_min;
+    P.active = active;
+    P.n_active = n_active;
+    P.level_cap = level_cap;
+    P.bricks = bricks;
+    P.words = state_words;
+    P.status = ctx->status;
+    dex::CavParams* M = new (std::nothrow) dex::CavParams();
+    if (!M) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    dex::fill_cav_params(*M, n_lambda, W, dv, c_kms);
+    int r = bind(ctx);
+    if (!r) {
+        cudaError_t e = dex::launch_cav_mips_build(ctx->stream, P, *M);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "cav_mips_build launch") : ok(ctx);
+    }
+    delete M;
+    return r;
+}
+
+int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv,
+                         float c_kms, const float* bricks, const unsigned long long* state_words,
+                         const int* block_offset, const int* active, const int* n_active, int capacity, int n_dir,
+                         const float* dirs, const float* weights, int n_band, const float* band, float i_bc,
+                         float* J, float* I, unsigned long long* seg_count)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_sparse_grid(ctx, nx, nz)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (int r = cav_lambda(ctx, n_lambda, dv, c_kms)) return r;
+    if (max_mip < 0 || max_mip > 4) return fail(ctx, DEX_ERR_ARG, "max_mip must be in [0, 4]");
+    const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
+    if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
+    if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
+    dex::HddaParams P{};
+    if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
+    P.n_band = -1;
+    if (band != nullptr && n_band >= 0) {
+        if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);
+        for (int q = 0; q < n_band; ++q) {
+            if (std::isnan(band[q]) || (q > 0 && band[q] < band[q - 1]))
+                return fail(ctx, DEX_ERR_ARG, "distance thresholds must be non-decreasing numbers");
+            P.band[q] = band[q];
+        }
+        P.n_band = n_band;
+    }
+    if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
+        return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(bricks, 16)) return fail(ctx, DEX_ERR_ARG, "bricks must be 16-byte aligned");
+    P.nx = nx;
+    P.nz = nz;
+    P.nbx = nx / DEX_BLOCK;
+    P.nbz = nz / DEX_BLOCK;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.chain = dex::chain_length(max_mip);
+    P.n_words = (int)dex_state_words(nx, nz);
+    P.cap_active = capacity;
+    P.n_cells = (long long)nx * nz;
+    P.bricks = bricks;
+    P.words = state_words;
+    P.block_offset = block_offset;
+    P.active = active;
+    P.n_active = n_active;
+    P.i_bc = i_bc;
+    P.J = J;
+    P.I = I;
+    P.seg_count = seg_count;
+    P.status = ctx->status;
+    dex::CavParams* M = new (std::nothrow) dex::CavParams();
+    if (!M) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    dex::fill_cav_params(*M, n_lambda, W, dv, c_kms);
+    int r = bind(ctx);
+    if (!r) {
+        cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
+        if (e == cudaSuccess && I)
+            e = cudaMemsetAsync(I, 0, sizeof(float) * (size_t)n_lambda * (size_t)n_dir * (size_t)P.n_cells,
+                                ctx->stream);
+        if (e == cudaSuccess) e = dex::launch_solve_cav(ctx->stream, P, *M);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "solve_cav launch") : ok(ctx);
+    }
+    delete M;
+    return r;
+}
+
 }  // extern "C"

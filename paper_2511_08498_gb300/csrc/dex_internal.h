@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "dex_common.cuh"
+#include "voigt.cuh"
 
 namespace dex {
 
@@ -74,7 +75,47 @@ cudaError_t launch_rates(cudaStream_t s, const AtomParams& P, long long n_cells,
 cudaError_t launch_se_solve(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T, const float* ne,
                             const float* nh, const double* jbar, double* pops);
 
+// Core-and-Voigt: per-cell parameter fields (device pointers) and per-wavelength constants
+struct CavFields {
+    const float* eta_star;
+    const float* chi_star;
+    const float* damping;
+    const float* vth;
+    const float* vx;
+    const float* vz;
+    const float* eta_c;
+    const float* chi_c;
+};
+
+struct CavParams {
+    VoigtCoef coef;
+    int n_lambda;
+    float dv[DEX_MAX_CAV_LAMBDA];   // wavelength offsets (km/s), padded to whole batches
+    float s[DEX_MAX_CAV_LAMBDA];    // lambda0 / lambda
+    float is2[DEX_MAX_CAV_LAMBDA];  // (lambda / lambda0)^2
+};
+
+struct CavMipParams {
+    int nx, nz, nbx, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active;
+    float thr_eta, thr_chi, chi_ds_min;
+    CavFields F;
+    const int* active;
+    const int* n_active;
+    const signed char* level_cap;
+    float* bricks;
+    unsigned long long* words;
+    unsigned int* status;
+};
+
+void fill_cav_params(CavParams& M, int n_lambda, int W, const float* dv, float c_kms);
+cudaError_t launch_block_layout(cudaStream_t s, int nbx, int nbz, int* block_offset, int* active, int* n_active);
+cudaError_t launch_cav_grid_build(cudaStream_t s, int nx, int nz, const CavFields& F, int* block_offset, int* active,
+                                  int* n_active);
+cudaError_t launch_cav_mips_build(cudaStream_t s, const CavMipParams& P, const CavParams& M);
+cudaError_t launch_solve_cav(cudaStream_t s, const HddaParams& P, const CavParams& M);
+
 int chain_length(int max_mip);
+cudaError_t launch_voigt(cudaStream_t s, long long n, const float* a, const float* x, float* h);
 cudaError_t launch_synth_static_line(cudaStream_t s, long long n_cells, int n_lambda, const float* chi_c,
                                      const float* s_c, const float* s_l, const float* ratio, const float* dld,
                                      const float* dlam, float* eta, float* chi);

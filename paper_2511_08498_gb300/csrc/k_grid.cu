@@ -115,6 +115,11 @@ cudaError_t launch_grid_build(cudaStream_t s, int nx, int nz, int n_lambda, cons
     k_block_flags<<<(unsigned)(nbx * nbz), 256, 0, s>>>(nx, nbx, n_cells, n_lambda, eta, chi, block_offset);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return launch_block_layout(s, nbx, nbz, block_offset, active, n_active);
+}
+
+cudaError_t launch_block_layout(cudaStream_t s, int nbx, int nbz, int* block_offset, int* active, int* n_active)
+{
     int log2P = 0;
     while ((1 << log2P) < nbx || (1 << log2P) < nbz) ++log2P;
     k_block_layout<<<1, 1024, 0, s>>>(nbx, nbz, log2P, block_offset, active, n_active);

@@ -16,7 +16,7 @@
 // block.  Every level of the chain is written as wavelength-batch records
 // (S, chi); the level goes into the packed 3-bit state words (0 = empty,
 // m + 1 = level m, 21 blocks per 64-bit word).
-#include "dex_internal.h"
+#include "vlm.cuh"
 
 namespace dex {
 
@@ -25,35 +25,6 @@ namespace {
 constexpr int kMaxLevels = 5;  // levels 0..4 of a 16 x 16 block
 
 __host__ __device__ constexpr int level_offset(int m) { return 341 - (341 >> (2 * m)); }
-
-struct GroupStat {
-    float val;
-    float iod;
-};
-
-// value and IoD of a 2x2 group at voxel side ds (ln_ds = ln ds)
-__device__ __forceinline__ GroupStat reduce_group(float g0, float g1, float g2, float g3, float ln_ds, bool log_mean)
-{
-    GroupStat r;
-    const int npos = (g0 > 0.0f) + (g1 > 0.0f) + (g2 > 0.0f) + (g3 > 0.0f);
-    const float lin = 0.25f * ((g0 + g1) + (g2 + g3));
-    if (npos == 4) {
-        const float L0 = logf(g0), L1 = logf(g1), L2 = logf(g2), L3 = logf(g3);
-        const float mL = 0.25f * ((L0 + L1) + (L2 + L3));
-        const float mu = mL + ln_ds;
-        const float d0 = L0 - mL, d1 = L1 - mL, d2 = L2 - mL, d3 = L3 - mL;
-        const float var = 0.25f * ((d0 * d0 + d1 * d1) + (d2 * d2 + d3 * d3));
-        r.iod = var == 0.0f ? 0.0f : fabsf(var / mu);
-        r.val = log_mean ? expf(mL) : lin;
-    } else if (npos == 0) {
-        r.iod = 0.0f;
-        r.val = 0.0f;
-    } else {
-        r.iod = __int_as_float(0x7f800000);
-        r.val = lin;
-    }
-    return r;
-}
 
 template <int W>
 __device__ __forceinline__ void store_record(float* rec, const float* e, const float* c)

@@ -17,4 +17,5 @@ from .atmospheres import (  # noqa: F401
     sparse_line_atmosphere,
     gaussian_field,
     random_medium,
+    dynamic_line_atmosphere,
 )

@@ -194,3 +194,66 @@ def random_medium(nx: int, nz: int, n_lambda: int, seed: int = SEED_BASE + 100,
         chi[l] = c
         eta[l] = e.astype(np.float32)
     return {"eta": eta, "chi": chi}
+
+
+C_KMS = 299792.458
+
+
+def dynamic_line_atmosphere(nx: int = 2048, nz: int = 1024, block: int = 16, n_lambda: int = 64,
+                            empty_frac: float = 0.4, seed: int = SEED_BASE + 3, sigma: float = 0.5,
+                            corr: float = 4.0, scale_height: float = 64.0, ratio_range=(1e2, 1e5),
+                            vmax: float = 50.0, vth_range=(5.0, 10.0), damping_range=(1e-3, 1e-1),
+                            lambda0_nm: float = 656.28):
+    """Moving-medium model: continuum + one Voigt line with a line-of-sight velocity field.
+
+    Same transition/continuum construction as ``sparse_line_atmosphere``.  Per cell:
+    velocity (vx, vz) in km/s = three seeded smooth Fourier modes plus two tanh shear
+    layers, rescaled so |v| <= ``vmax``; thermal (Doppler) width v_th in km/s, smooth
+    uniform over ``vth_range``; damping a, log-uniform over ``damping_range`` as a smooth
+    field; line strength ``chi_star`` (per cell, per km/s) = r chi_c sqrt(pi) v_th, so that
+    the undamped line-centre opacity is r chi_c with r log-uniform over ``ratio_range``;
+    ``eta_star`` = chi_star S_l.  Wavelengths are velocity offsets ``dv`` (km/s) from the
+    rest wavelength ``lambda0_nm``, uniform over +-(vmax + 3 max v_th).
+    """
+    if nx % block or nz % block:
+        raise ValueError("model extent must be a whole number of blocks")
+    rng = np.random.default_rng(seed)
+    z_tr, frac = _transition_height(nx, nz, block, empty_frac, rng)
+    x = np.arange(nx, dtype=np.float64) + 0.5
+    z = np.arange(nz, dtype=np.float64) + 0.5
+    X, Z = np.meshgrid(x, z)
+    depth = z_tr[None, :] - z[:, None]
+    inside = depth > 0.0
+    ln = lognormal_field((nz, nx), sigma, corr, rng)
+    chi_c = np.where(inside, 1e-3 * np.exp(np.minimum(depth, 60.0 * scale_height) / scale_height) * ln, 0.0)
+    d_pos = np.maximum(depth, 0.0)
+    s_c = np.where(inside, 1.0 + d_pos / 256.0 + 0.5 * np.sin(2.0 * np.pi * X / 64.0) * np.exp(-d_pos / 40.0), 0.0)
+    s_l = np.where(inside, s_c * (0.3 + 0.7 * (1.0 - np.exp(-d_pos / 24.0))), 0.0)
+    vel = []
+    for _ in range(2):
+        f = np.zeros((nz, nx))
+        for _m in range(3):
+            kx, kz = rng.uniform(-4, 4, 2) * 2 * np.pi / np.array([nx, nz])
+            f += rng.uniform(0.3, 1.0) * np.sin(kx * X + kz * Z + rng.uniform(0, 2 * np.pi))
+        vel.append(f)
+    z1, z2 = rng.uniform(0.2, 0.8, 2) * nz
+    vel[0] = vel[0] + 1.5 * np.tanh((Z - z1) / 6.0) - 1.5 * np.tanh((Z - z2) / 6.0)
+    vx, vz = vel
+    mag = np.sqrt(vx * vx + vz * vz)
+    scale = vmax / max(float(mag.max()), 1e-30)
+    vx, vz = vx * scale, vz * scale
+    vth = vth_range[0] + (vth_range[1] - vth_range[0]) * smooth_uniform_field((nz, nx), 32.0, rng)
+    la0, la1 = np.log10(damping_range[0]), np.log10(damping_range[1])
+    damping = 10.0 ** (la0 + (la1 - la0) * smooth_uniform_field((nz, nx), 32.0, rng))
+    lr0, lr1 = np.log10(ratio_range[0]), np.log10(ratio_range[1])
+    ratio = 10.0 ** (lr0 + (lr1 - lr0) * smooth_uniform_field((nz, nx), 32.0, rng))
+    chi_star = ratio * chi_c * np.sqrt(np.pi) * vth
+    half = vmax + 3.0 * vth_range[1]
+    dv = np.linspace(-half, half, n_lambda)
+    f32 = lambda a: np.where(inside, a, 0.0).astype(np.float32)
+    return {
+        "chi_star": f32(chi_star), "eta_star": f32(chi_star * s_l), "damping": f32(damping),
+        "vth": f32(vth), "vx": f32(vx), "vz": f32(vz), "chi_c": f32(chi_c), "eta_c": f32(chi_c * s_c),
+        "dv": dv.astype(np.float32), "lambda0_nm": float(lambda0_nm), "c_kms": C_KMS,
+        "empty_block_frac": frac, "block": block,
+    }

@@ -1,0 +1,112 @@
+"""Core-and-Voigt (moving medium) GPU path vs the float64 oracle.
+
+Tolerances, derived from the arithmetic:
+* Voigt function (float32, HUM1WEI24 with the continued-fraction band) vs the same
+  scheme in float64: relative 2e-5 where |x| + a < 2 or >= 5 (no cancellation),
+  and 1e-3 for 2 <= |x| + a < 5 with damping a >= 1e-3, where Weideman's sum cancels
+  O(1) terms down to H ~ 1e-5 (measured worst case 6.5e-4 at a = 1e-3).
+* CaV intensities vs the float64 oracle running the same scheme: eta and chi inherit
+  at most the Voigt function's relative error, so I and J are compared at 1e-3.
+* Block levels: exact away from thresholds (checked on the oracle's side).
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import cav, mips as omips, voigt
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b) / np.maximum(np.abs(b), 1e-30)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2511_08498_gb300 import api
+    return api.Context(0)
+
+
+def test_voigt_kernel(ctx):
+    from paper_2511_08498_gb300 import api
+    x = np.concatenate([np.linspace(-40, 40, 40001), np.geomspace(40, 2000, 500)]).astype(np.float32)
+    for a in np.geomspace(1e-3, 1e-1, 5).astype(np.float32):
+        A = np.full_like(x, a)
+        h = api.voigt(ctx, torch.from_numpy(A).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
+        ref = voigt.voigt_h(A.astype(np.float64), x.astype(np.float64), method="hum1wei24_cf")
+        e = rel(h, ref)
+        s = np.abs(x) + a
+        assert e[(s < 2) | (s >= 5)].max() < 2e-5, (a, e[(s < 2) | (s >= 5)].max())
+        assert e.max() < 1e-3, (a, e.max())
+    # special values
+    z = torch.zeros(3, device="cuda")
+    h0 = api.voigt(ctx, z, torch.tensor([0.0, 1.0, 2.0], device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(h0, np.exp(-np.array([0.0, 1.0, 4.0])), rtol=2e-5)
+
+
+def model(nx=128, nz=96, n_lambda=16, seed=600):
+    return synth.dynamic_line_atmosphere(nx, nz, n_lambda=n_lambda, seed=synth.SEED_BASE + seed)
+
+
+def gpu_cav(ctx, m, W, max_mip, iod, dirs, w, band=None, cm=0.25):
+    from paper_2511_08498_gb300 import api
+    nz, nx = m["chi_c"].shape
+    f = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda() for k in api.CAV_FIELDS}
+    grid = api.cav_grid_build(ctx, nx, nz, f)
+    mp = api.cav_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, cm)
+    J, I, seg = api.formal_solve_cav(ctx, grid, mp, dirs, w, band=band, want_intensity=True, count_segments=True)
+    ctx.check()
+    return grid, mp, J, I, seg
+
+
+def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei24_cf", stats=False):
+    P0 = cav.param_arrays(m)
+    chain = cav.param_chain(P0, max_mip)
+    empty = omips.block_empty(np.stack([m["eta_star"], m["eta_c"]]), np.stack([m["chi_star"], m["chi_c"]]), 16)
+    if max_mip > 0:
+        lev, st = cav.block_levels(chain, m["dv"], m["c_kms"], empty, 16, W, iod, iod, cm, stats=True)
+    else:
+        lev, st = omips.block_levels([], empty, 16, W, n_lambda=m["dv"].size), []
+    probes = omips.probes_of_blocks(empty, 16)
+    J, I = cav.formal_solve(chain, lev, 16, W, m["dv"], m["c_kms"], dirs, w, probes, band=band, method=method,
+                            want_intensity=True)
+    return dict(lev=lev, stats=st, probes=probes, J=J, I=I, empty=empty)
+
+
+@pytest.mark.parametrize("max_mip,iod,band", [(0, 1.0, None), (2, 1.0, None), (3, 1e9, [5.3, 21.7, 40.2]),
+                                              (2, 1e-2, [3.1])])
+def test_cav_solve_matches_oracle(ctx, max_mip, iod, band):
+    from paper_2511_08498_gb300 import api
+    m = model()
+    dirs, w = synth.directions(8)
+    grid, mp, J, I, seg = gpu_cav(ctx, m, 8, max_mip, iod, dirs, w, band=band)
+    o = oracle_cav(m, 8, max_mip, iod, dirs, w, band=band)
+    nbz, nbx = o["empty"].shape
+    assert grid.n_active() == int((~o["empty"]).sum())
+    glev = api.unpack_states(mp.words.cpu().numpy(), nbz * nbx).reshape(o["lev"].shape)
+    np.testing.assert_array_equal(glev, o["lev"])
+    p = o["probes"]
+    eI = rel(I.cpu().numpy()[:, :, p], o["I"])
+    eJ = rel(J.cpu().numpy()[:, p], o["J"])
+    assert eI.max() < 1e-3, f"I max rel err {eI.max():.3e}"
+    assert eJ.max() < 1e-3, f"J max rel err {eJ.max():.3e}"
+
+
+def test_cav_static_limit_is_the_static_line(ctx):
+    """With v = 0, negligible damping and c -> infinity, CaV reduces to the static
+    Gaussian line: the same J as the static-line path on the same opacities."""
+    m = model(seed=610)
+    m = dict(m)
+    m["vx"] = np.zeros_like(m["vx"])
+    m["vz"] = np.zeros_like(m["vz"])
+    m["damping"] = np.where(m["chi_c"] > 0, 1e-7, 0.0).astype(np.float32)
+    m["c_kms"] = 1e30
+    dirs, w = synth.directions(8)
+    _, _, J, _, _ = gpu_cav(ctx, m, 8, 0, 1.0, dirs, w)
+    o = oracle_cav(m, 8, 0, 1.0, dirs, w, method="exact")
+    assert rel(J.cpu().numpy()[:, o["probes"]], o["J"]).max() < 1e-3

@@ -48,3 +48,16 @@ def test_hum1wei24_accuracy_over_the_line():
         approx = voigt.voigt_h(a, x, method="hum1wei24")
         worst = max(worst, float(np.max(np.abs(approx - ref) / ref)))
     assert worst < 1e-4, worst
+
+
+def test_continued_fraction_band_accuracy():
+    # the GPU's variant: exact to the Weideman branch's accuracy in |x| + a < 5, and
+    # to the continued fraction's in the band 5 <= |x| + a < 15 (better than region I)
+    x = np.concatenate([np.linspace(-40, 40, 80001)])
+    for a in np.geomspace(1e-3, 1e-1, 5):
+        ref = voigt.voigt_h(a, x)
+        v = voigt.voigt_h(a, x, method="hum1wei24_cf")
+        err = np.abs(v - ref) / ref
+        band = (np.abs(x) + a >= 5) & (np.abs(x) + a < 15)
+        assert err[band].max() < 1e-6, (a, err[band].max())
+        assert err.max() < 6e-5
