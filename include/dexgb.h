@@ -355,6 +355,75 @@ int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int 
                          const float* dirs, const float* weights, int n_band, const float* band, float i_bc,
                          float* J, float* I, unsigned long long* seg_count);
 
+/* --------------------------------------------------- velocity interpolation --
+ *
+ * Section 3.1 with the line model above: every MIP voxel (MIP 0 included)
+ * stores, per wavelength batch, its mean velocity, V = the largest speed of its
+ * MIP-0 cells, and eta, chi at DEX_VEL_SAMPLES projected velocities
+ * v_s = -V + 2 V s / (DEX_VEL_SAMPLES - 1) (each the mean over the voxel's MIP-0
+ * cells of the cell's eta, chi at u = dv + v_s).  Along a ray the voxel's eta,
+ * chi are interpolated linearly at the projected mean velocity, clamped to
+ * [-V, V].  Block levels come from Eq. IoD on the rest-frame (projected
+ * velocity 0) values.  Record: 4 + DEX_VEL_SAMPLES * 2W floats
+ * (v_x, v_z, V, 0, then for each grid velocity eta[W], chi[W]).
+ */
+#define DEX_VEL_SAMPLES 8
+
+/* Floats of the velocity-grid bricks: n_batch * capacity * chain * (4 + 16 W). */
+size_t dex_vel_brick_floats(int capacity, int n_lambda, int W, int max_mip);
+
+/* Build the velocity-grid MIP chains and the per-batch block levels; arguments as
+ * dex_cav_mips_build (bricks sized by dex_vel_brick_floats). */
+int dex_vel_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int n_lambda, int W,
+                       const float* dv, float c_kms, const int* active, const int* n_active, int capacity,
+                       const dex_vlm_params* params, const signed char* level_cap, float* bricks,
+                       unsigned long long* state_words);
+
+/* Formal solution with velocity interpolation; arguments as dex_formal_solve_hdda. */
+int dex_formal_solve_velinterp(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
+                               const unsigned long long* state_words, const int* block_offset, const int* active,
+                               const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
+                               int n_band, const float* band, float i_bc, float* J, float* I,
+                               unsigned long long* seg_count);
+
+/* ---------------------------------------------------- batched atmospheres --
+ *
+ * Many independent atmospheres solved by one persistent launch: a fixed grid of
+ * CTAs pulls work items (atmosphere, wavelength batch, active block) from a
+ * device counter until none are left; each item is the 256-probe block solve of
+ * dex_formal_solve_hdda (static records).  The atmospheres share the batch
+ * width W and differ in size, wavelengths, quadrature and sparsity.
+ */
+#define DEX_MAX_BATCH_ATM 32
+
+typedef struct {
+    int nx, nz, n_lambda, max_mip, capacity;      /* as for dex_formal_solve_hdda          */
+    const float* bricks;                          /* device, from dex_mips_build           */
+    const unsigned long long* state_words;        /* device                                */
+    const int* block_offset;                      /* device, from dex_grid_build           */
+    const int* active;                            /* device                                */
+    const int* n_active;                          /* device                                */
+    int n_dir;                                    /* 1 .. DEX_MAX_DIRS                     */
+    const float* dirs;                            /* DEVICE [n_dir][2] unit vectors         */
+    const float* weights;                         /* DEVICE [n_dir]                        */
+    int n_band;                                   /* distance limits as dex_formal_solve_hdda; */
+    float band[4];                                /*   n_band < 0: none                    */
+    float i_bc;
+    float* J;                                     /* device [n_lambda][nz][nx], zeroed here */
+} dex_batch_item;
+
+/*
+ * Solve n_atm (<= DEX_MAX_BATCH_ATM) atmospheres in one persistent launch.
+ *   atms     host [n_atm] descriptors (device pointers inside)
+ *   ctas     persistent grid size (0: 3 per SM)
+ *   queue    device scratch: one unsigned int, the work counter (reset by the call)
+ *   done_ns  device [n_atm] or NULL: completion time of each atmosphere's last item
+ *            (GPU global timer, ns), start_ns device [1] or NULL: the earliest CTA start
+ * Every J is zeroed by the call, then written at the probe cells.
+ */
+int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, int ctas, unsigned int* queue,
+                    unsigned long long* done_ns, unsigned long long* start_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,14 +74,22 @@ def laplace_cf(x, y, n_terms: int = 8):
 
 def hum1wei24_cf(x, y):
     """w(x + i y): Humlicek region I for s >= 15, continued fraction for 5 <= s < 15,
-    Weideman-24 for s < 5 (s = |x| + y)."""
+    Weideman-24 for s < 5 (s = |x| + y).  The branch is chosen with s computed in
+    float32, the precision in which the GPU kernel takes the same decision; the
+    values are float64."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     x, y = np.broadcast_arrays(x, y)
-    out = hum1wei24(x, y)
-    s = np.abs(x) + y
-    band = (s >= 5.0) & (s < 15.0)
+    s32 = np.abs(x).astype(np.float32) + y.astype(np.float32)
+    z = x + 1j * y
+    out = np.empty(x.shape, dtype=np.complex128)
+    far = s32 >= np.float32(15.0)
+    band = (s32 >= np.float32(5.0)) & ~far
+    near = ~(far | band)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        out[far] = 1j * z[far] / (np.sqrt(np.pi) * (z[far] * z[far] - 0.5))
     out[band] = laplace_cf(x[band], y[band])
+    out[near] = hum1wei24(x[near], y[near])   # s < 5 < 15: the Weideman branch
     return out
 
 

@@ -55,6 +55,13 @@ PROTOTYPES = {
     "dex_formal_solve_cav": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_fp, c_float, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float,
                                      c_void_p, c_void_p, c_void_p]),
+    "dex_vel_brick_floats": (c_size_t, [c_int, c_int, c_int, c_int]),
+    "dex_vel_mips_build": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_fp, c_float, c_void_p, c_void_p,
+                                   c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dex_formal_solve_velinterp": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                           c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float,
+                                           c_void_p, c_void_p, c_void_p]),
+    "dex_batch_solve": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
 }
 
 

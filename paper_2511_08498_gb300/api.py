@@ -451,3 +451,101 @@ def formal_solve_cav(ctx: Context, grid: SparseGrid, mips: CavMips, dirs, weight
         mips.capacity, d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
         None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
     return J, I, seg
+
+
+# ------------------------------------------------- velocity interpolation --
+
+VEL_SAMPLES = 8
+
+
+def vel_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: float, W: int, max_mip: int,
+                   iod_eta: float, iod_chi: float, chi_ds_min: float = 0.25, level_cap=None, capacity=None,
+                   out: CavMips | None = None):
+    """Velocity-grid MIP chains + rest-frame VLM levels (``dex_vel_mips_build``)."""
+    cap = grid.n_blocks if capacity is None else int(capacity)
+    dvh = np.ascontiguousarray(np.asarray(dv, dtype=np.float32))
+    n_batch = -(-dvh.size // W)
+    dev = fields["chi_c"].device
+    if out is None:
+        nf = int(lib().dex_vel_brick_floats(cap, dvh.size, W, max_mip))
+        out = CavMips(torch.empty(max(nf, 4), dtype=torch.float32, device=dev),
+                      torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=dev),
+                      W, max_mip, dvh, c_kms, cap)
+    f = CavFields.from_tensors(fields)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0)
+    fp = ctypes.POINTER(ctypes.c_float)
+    ctx._rc(lib().dex_vel_mips_build(ctx.handle, grid.nx, grid.nz, ctypes.byref(f), dvh.size, W,
+                                     dvh.ctypes.data_as(fp), float(c_kms), _ptr(grid.active), _ptr(grid.n_active_dev),
+                                     cap, ctypes.byref(p), _ptr(level_cap), _ptr(out.bricks), _ptr(out.words)))
+    return out
+
+
+def formal_solve_velinterp(ctx: Context, grid: SparseGrid, mips: CavMips, dirs, weights, band=None,
+                           i_bc: float = 0.0, want_intensity: bool = False, count_segments: bool = False,
+                           J: torch.Tensor | None = None):
+    """Velocity-interpolation solve (``dex_formal_solve_velinterp``)."""
+    d, w = _quadrature(dirs, weights)
+    dev = mips.bricks.device
+    n_cells = grid.nx * grid.nz
+    L = mips.n_lambda
+    if J is None:
+        J = torch.empty((L, n_cells), dtype=torch.float32, device=dev)
+    I = torch.empty((L, d.shape[0], n_cells), dtype=torch.float32, device=dev) if want_intensity else None
+    seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
+    fp = ctypes.POINTER(ctypes.c_float)
+    b = None if band is None else _host_f32(band).reshape(-1)
+    ctx._rc(lib().dex_formal_solve_velinterp(
+        ctx.handle, grid.nx, grid.nz, L, mips.W, mips.max_mip, _ptr(mips.bricks), _ptr(mips.words),
+        _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev), mips.capacity, d.shape[0],
+        d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
+        None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+    return J, I, seg
+
+
+# ---------------------------------------------------- batched atmospheres --
+
+MAX_BATCH_ATM = 32
+
+
+class BatchItem(ctypes.Structure):
+    """``dex_batch_item``: one atmosphere of a batched solve (device pointers inside)."""
+    _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("n_lambda", ctypes.c_int), ("max_mip", ctypes.c_int),
+                ("capacity", ctypes.c_int), ("bricks", ctypes.c_void_p), ("state_words", ctypes.c_void_p),
+                ("block_offset", ctypes.c_void_p), ("active", ctypes.c_void_p), ("n_active", ctypes.c_void_p),
+                ("n_dir", ctypes.c_int), ("dirs", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("n_band", ctypes.c_int), ("band", ctypes.c_float * 4), ("i_bc", ctypes.c_float),
+                ("J", ctypes.c_void_p)]
+
+
+def batch_item(grid: SparseGrid, mips: Mips, dirs_dev: torch.Tensor, weights_dev: torch.Tensor, J: torch.Tensor,
+               band=None, i_bc: float = 0.0) -> BatchItem:
+    it = BatchItem()
+    it.nx, it.nz, it.n_lambda, it.max_mip, it.capacity = grid.nx, grid.nz, mips.n_lambda, mips.max_mip, mips.capacity
+    it.bricks, it.state_words = mips.bricks.data_ptr(), mips.words.data_ptr()
+    it.block_offset, it.active, it.n_active = (grid.block_offset.data_ptr(), grid.active.data_ptr(),
+                                               grid.n_active_dev.data_ptr())
+    it.n_dir = int(dirs_dev.shape[0])
+    it.dirs, it.weights = dirs_dev.data_ptr(), weights_dev.data_ptr()
+    b = [] if band is None else list(band)
+    it.n_band = -1 if band is None else len(b)
+    for q, v in enumerate(b[:4]):
+        it.band[q] = float(v)
+    it.i_bc = float(i_bc)
+    it.J = J.data_ptr()
+    return it
+
+
+def batch_solve(ctx: Context, items, W: int, ctas: int = 0, queue: torch.Tensor | None = None,
+                timing: bool = False):
+    """One persistent launch over all atmospheres (``dex_batch_solve``).
+
+    Returns ``(done_ns, start_ns)`` device tensors when ``timing`` (else ``(None, None)``)."""
+    n = len(items)
+    arr = (BatchItem * n)(*items)
+    dev = torch.device("cuda", ctx.device)
+    if queue is None:
+        queue = torch.zeros(1, dtype=torch.int32, device=dev)
+    done = torch.zeros(n, dtype=torch.int64, device=dev) if timing else None
+    start = torch.zeros(1, dtype=torch.int64, device=dev) if timing else None
+    ctx._rc(lib().dex_batch_solve(ctx.handle, n, arr, W, int(ctas), _ptr(queue), _ptr(done), _ptr(start)))
+    return done, start

@@ -1,0 +1,175 @@
+"""Autotuning and reporting of the batched (many-atmosphere) solve.
+
+``tune_batch`` times the persistent launch for several grid sizes (CTAs per SM)
+and returns the fastest; ``batch_report`` builds a seeded set of independent
+atmospheres, then times one step three ways -- a sequential launch per
+atmosphere, one persistent launch, and the whole step (line synthesis, grids,
+MIPs and the persistent solve) replayed from a captured CUDA graph -- and writes
+a JSON report with aggregate dense-equivalent segment throughput and
+per-atmosphere completion times.
+
+Usage: python -m paper_2511_08498_gb300.autotune [--scale S] [--out FILE]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+
+import numpy as np
+import torch
+
+from . import api
+
+DISTANCE_LIMITS = [6.0, 24.0, 96.0]
+
+
+def _time(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def tune_batch(ctx, items, W, ctas_per_sm=(1, 2, 3, 4), reps=3):
+    """Fastest persistent grid size: returns ``{"best_ctas", "times_ms"}``."""
+    sms = torch.cuda.get_device_properties(ctx.device).multi_processor_count
+    queue = torch.zeros(1, dtype=torch.int32, device=torch.device("cuda", ctx.device))
+    times = {}
+    for k in ctas_per_sm:
+        times[k * sms] = _time(lambda: api.batch_solve(ctx, items, W, ctas=k * sms, queue=queue), reps)
+    best = min(times, key=times.get)
+    return {"best_ctas": int(best), "times_ms": {str(k): v for k, v in times.items()}}
+
+
+class Atmosphere:
+    """Device-resident model parameters and buffers of one atmosphere of the batch."""
+
+    def __init__(self, ctx, spec, W, iod):
+        import synth
+        self.spec, self.ctx, self.W, self.iod = spec, ctx, W, iod
+        m = synth.sparse_line_atmosphere(spec["nx"], spec["nz"], n_lambda=spec["n_lambda"],
+                                         empty_frac=spec["empty_frac"], seed=spec["seed"])
+        self.params = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda()
+                       for k in ("chi_c", "s_c", "s_l", "ratio", "dld", "dlam")}
+        n = spec["nx"] * spec["nz"]
+        self.eta = torch.empty((spec["n_lambda"], n), device="cuda")
+        self.chi = torch.empty_like(self.eta)
+        self.J = torch.empty_like(self.eta)
+        dirs, w = synth.directions(spec["n_dir"])
+        self.dirs, self.w = dirs, w
+        self.dirs_dev, self.w_dev = torch.from_numpy(dirs).cuda(), torch.from_numpy(w).cuda()
+        self.grid = None
+        self.mips = None
+        self.build()
+
+    def build(self):
+        p = self.params
+        api.synth_static_line(self.ctx, p["chi_c"], p["s_c"], p["s_l"], p["ratio"], p["dld"], p["dlam"],
+                              eta=self.eta, chi=self.chi)
+        self.grid = api.grid_build(self.ctx, self.spec["nx"], self.spec["nz"], self.eta, self.chi, out=self.grid)
+        self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, self.W, 3, self.iod, self.iod, 0.25,
+                                   out=self.mips)
+
+    def solve(self):
+        api.formal_solve_hdda(self.ctx, self.grid, self.mips, self.dirs, self.w, J=self.J, band=DISTANCE_LIMITS)
+
+    def item(self):
+        return api.batch_item(self.grid, self.mips, self.dirs_dev, self.w_dev, self.J, band=DISTANCE_LIMITS)
+
+    def dense_seg_lambda(self):
+        """Full-resolution voxel segments x wavelengths of this atmosphere's probes (one plain pass)."""
+        g = self.grid
+        act = torch.nonzero(g.block_offset >= 0).reshape(-1)
+        bx, bz = act % g.nbx, act // g.nbx
+        loc = torch.arange(256, device="cuda")
+        cells = ((bz[:, None] * 16 + loc[None, :] // 16) * g.nx + bx[:, None] * 16 + loc[None, :] % 16)
+        cells = cells.reshape(-1).to(torch.int32)
+        planes = api.pack_planes(self.ctx, self.eta, self.chi, self.W)
+        _, _, seg = api.formal_solve_dense(self.ctx, g.nx, g.nz, self.spec["n_lambda"], self.W, planes, self.dirs,
+                                           self.w, probes=cells, count_segments=True)
+        return int(seg.item()) * self.W
+
+
+def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3):
+    import synth
+    ctx = api.Context(0)
+    specs = synth.batch_specs(n_atm, scale=scale) if seed is None else synth.batch_specs(n_atm, seed=seed, scale=scale)
+    atms = [Atmosphere(ctx, sp, W, iod) for sp in specs]
+    torch.cuda.synchronize()
+    dense = [a.dense_seg_lambda() for a in atms]
+    items = [a.item() for a in atms]
+    tuned = tune_batch(ctx, items, W, reps=reps)
+    ctas = tuned["best_ctas"]
+    queue = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    # sequential: one launch per atmosphere (solve only), and the whole step
+    t_seq = _time(lambda: [a.solve() for a in atms], reps)
+    t_pers = _time(lambda: api.batch_solve(ctx, items, W, ctas=ctas, queue=queue), reps)
+
+    def whole_step():
+        for a in atms:
+            a.build()
+        api.batch_solve(ctx, items, W, ctas=ctas, queue=queue)
+
+    t_step_eager = _time(whole_step, reps)
+    # capture the whole step in a CUDA graph (the library calls enqueue on the capture stream)
+    g = torch.cuda.CUDAGraph()
+    old = ctx.stream
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ctx.set_stream(s)
+        whole_step()          # warm up on the side stream (kernel attributes, lazy loading)
+        s.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            whole_step()
+    ctx.set_stream(old)
+    torch.cuda.current_stream().wait_stream(s)
+    t_graph = _time(g.replay, reps)
+    done, start = api.batch_solve(ctx, items, W, ctas=ctas, queue=queue, timing=True)
+    ctx.check()
+    per_atm_ms = ((done.cpu().numpy() - int(start.item())) / 1e6).tolist()
+    total_dense = float(sum(dense))
+    return {
+        "workload": f"{n_atm} independent sparse static-line atmospheres (scale {scale}), VLM mip 0-3, "
+                    f"IoD threshold {iod:g}, distance limits {DISTANCE_LIMITS}, W={W}",
+        "atmospheres": specs,
+        "dense_seg_lambda": dense,
+        "tuning": tuned,
+        "sequential_solve_ms": t_seq,
+        "persistent_solve_ms": t_pers,
+        "persistent_speedup_vs_sequential": t_seq / t_pers,
+        "step_eager_ms": t_step_eager,
+        "step_graph_ms": t_graph,
+        "aggregate_seg_lambda_per_s": {"sequential": total_dense / (t_seq / 1e3),
+                                       "persistent": total_dense / (t_pers / 1e3),
+                                       "graph_step": total_dense / (t_graph / 1e3)},
+        "per_atmosphere_done_ms": per_atm_ms,
+    }
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--n-atm", type=int, default=24)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args(argv)
+    rep = batch_report(scale=args.scale, n_atm=args.n_atm)
+    s = json.dumps(rep)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(s + "\n")
+    print(s)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -377,11 +377,11 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
     return ok(ctx);
 }
 
-int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
-                          const unsigned long long* state_words, const int* block_offset, const int* active,
-                          const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
-                          int n_band, const float* band, float i_bc, float* J, float* I,
-                          unsigned long long* seg_count)
+static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, int W, int max_mip,
+                        const float* bricks, const unsigned long long* state_words, const int* block_offset,
+                        const int* active, const int* n_active, int capacity, int n_dir, const float* dirs,
+                        const float* weights, int n_band, const float* band, float i_bc, float* J, float* I,
+                        unsigned long long* seg_count)
 {
     if (!ctx) return DEX_ERR_ARG;
     if (int r = check_sparse_grid(ctx, nx, nz)) return r;
@@ -431,9 +431,19 @@ int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int
     cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
     if (e == cudaSuccess && I)
         e = cudaMemsetAsync(I, 0, sizeof(float) * (size_t)n_lambda * (size_t)n_dir * (size_t)P.n_cells, ctx->stream);
-    if (e == cudaSuccess) e = dex::launch_solve_hdda(ctx->stream, P);
+    if (e == cudaSuccess)
+        e = kind == 2 ? dex::launch_solve_velinterp(ctx->stream, P) : dex::launch_solve_hdda(ctx->stream, P);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_hdda launch");
     return ok(ctx);
+}
+int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
+                          const unsigned long long* state_words, const int* block_offset, const int* active,
+                          const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
+                          int n_band, const float* band, float i_bc, float* J, float* I,
+                          unsigned long long* seg_count)
+{
+    return solve_sparse(ctx, 0, nx, nz, n_lambda, W, max_mip, bricks, state_words, block_offset, active, n_active,
+                        capacity, n_dir, dirs, weights, n_band, band, i_bc, J, I, seg_count);
 }
 
 int dex_lte_populations(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature, const float* nh,
@@ -563,10 +573,10 @@ size_t dex_cav_brick_floats(int capacity, int max_mip)
     return (size_t)capacity * (size_t)dex::chain_length(max_mip) * 8;
 }
 
-int dex_cav_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int n_lambda, int W,
-                       const float* dv, float c_kms, const int* active, const int* n_active, int capacity,
-                       const dex_vlm_params* params, const signed char* level_cap, float* bricks,
-                       unsigned long long* state_words)
+static int moving_mips_build(dex_ctx* ctx, bool velgrid, int nx, int nz, const dex_cav_fields* fields,
+                             int n_lambda, int W, const float* dv, float c_kms, const int* active,
+                             const int* n_active, int capacity, const dex_vlm_params* params,
+                             const signed char* level_cap, float* bricks, unsigned long long* state_words)
 {
     if (!ctx) return DEX_ERR_ARG;
     if (int r = check_sparse_grid(ctx, nx, nz)) return r;
@@ -607,11 +617,37 @@ int dex_cav_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* field
     dex::fill_cav_params(*M, n_lambda, W, dv, c_kms);
     int r = bind(ctx);
     if (!r) {
-        cudaError_t e = dex::launch_cav_mips_build(ctx->stream, P, *M);
-        r = e != cudaSuccess ? cuda_fail(ctx, e, "cav_mips_build launch") : ok(ctx);
+        cudaError_t e = velgrid ? dex::launch_vel_mips_build(ctx->stream, P, *M)
+                                : dex::launch_cav_mips_build(ctx->stream, P, *M);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "mips build launch") : ok(ctx);
     }
     delete M;
     return r;
+}
+
+int dex_cav_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int n_lambda, int W,
+                       const float* dv, float c_kms, const int* active, const int* n_active, int capacity,
+                       const dex_vlm_params* params, const signed char* level_cap, float* bricks,
+                       unsigned long long* state_words)
+{
+    return moving_mips_build(ctx, false, nx, nz, fields, n_lambda, W, dv, c_kms, active, n_active, capacity, params,
+                             level_cap, bricks, state_words);
+}
+
+size_t dex_vel_brick_floats(int capacity, int n_lambda, int W, int max_mip)
+{
+    if (capacity < 0 || n_lambda < 0 || !valid_W(W) || max_mip < 0 || max_mip > 4) return 0;
+    const size_t n_batch = (size_t)((n_lambda + W - 1) / W);
+    return n_batch * (size_t)capacity * (size_t)dex::chain_length(max_mip) * (size_t)dex::vel_record_floats(W);
+}
+
+int dex_vel_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* fields, int n_lambda, int W,
+                       const float* dv, float c_kms, const int* active, const int* n_active, int capacity,
+                       const dex_vlm_params* params, const signed char* level_cap, float* bricks,
+                       unsigned long long* state_words)
+{
+    return moving_mips_build(ctx, true, nx, nz, fields, n_lambda, W, dv, c_kms, active, n_active, capacity, params,
+                             level_cap, bricks, state_words);
 }
 
 int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv,
@@ -677,6 +713,113 @@ int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int 
         r = e != cudaSuccess ? cuda_fail(ctx, e, "solve_cav launch") : ok(ctx);
     }
     delete M;
+    return r;
+}
+
+int dex_formal_solve_velinterp(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
+                               const unsigned long long* state_words, const int* block_offset, const int* active,
+                               const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
+                               int n_band, const float* band, float i_bc, float* J, float* I,
+                               unsigned long long* seg_count)
+{
+    return solve_sparse(ctx, 2, nx, nz, n_lambda, W, max_mip, bricks, state_words, block_offset, active, n_active,
+                        capacity, n_dir, dirs, weights, n_band, band, i_bc, J, I, seg_count);
+}
+
+// Validate the batch descriptors and fill the launch parameters (no launch).
+static int fill_batch(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, dex::BatchParams& P,
+                      size_t& max_words)
+{
+    if (n_atm < 1 || n_atm > DEX_MAX_BATCH_ATM)
+        return fail(ctx, DEX_ERR_ARG, "n_atm must be in [1, %d], got %d", DEX_MAX_BATCH_ATM, n_atm);
+    if (!atms) return fail(ctx, DEX_ERR_ARG, "atms (host) required");
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    long long base = 0;
+    max_words = 0;
+    P.n_atm = n_atm;
+    for (int a = 0; a < n_atm; ++a) {
+        const dex_batch_item& it = atms[a];
+        if (int r = check_sparse_grid(ctx, it.nx, it.nz)) return r;
+        if (it.n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: n_lambda must be >= 1", a);
+        if (it.max_mip < 0 || it.max_mip > 4) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bad max_mip", a);
+        const int nb = (it.nx / DEX_BLOCK) * (it.nz / DEX_BLOCK);
+        if (it.capacity < 0 || it.capacity > nb) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bad capacity", a);
+        if (it.n_dir < 1 || it.n_dir > DEX_MAX_DIRS) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bad n_dir", a);
+        if (!it.bricks || !it.state_words || !it.block_offset || !it.active || !it.n_active || !it.dirs ||
+            !it.weights || !it.J)
+            return fail(ctx, DEX_ERR_ARG, "atmosphere %d: null buffer", a);
+        if (!aligned(it.bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bricks misaligned", a);
+        if (it.n_band > 4) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: at most 4 distance thresholds", a);
+        if (!std::isfinite(it.i_bc)) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: i_bc not finite", a);
+        dex::AtmDesc& A = P.atm[a];
+        A.nx = it.nx;
+        A.nz = it.nz;
+        A.nbx = it.nx / DEX_BLOCK;
+        A.nbz = it.nz / DEX_BLOCK;
+        A.n_lambda = it.n_lambda;
+        A.chain = dex::chain_length(it.max_mip);
+        A.n_words = (int)dex_state_words(it.nx, it.nz);
+        A.cap_active = it.capacity;
+        A.n_dir = it.n_dir;
+        A.n_band = it.n_band < 0 ? -1 : it.n_band;
+        for (int q = 0; q < 4; ++q) A.band[q] = it.band[q];
+        for (int q = 1; q < (A.n_band > 0 ? A.n_band : 0); ++q)
+            if (!(A.band[q] >= A.band[q - 1])) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bad thresholds", a);
+        A.i_bc = it.i_bc;
+        A.item_base = base;
+        A.bricks = it.bricks;
+        A.words = it.state_words;
+        A.block_offset = it.block_offset;
+        A.active = it.active;
+        A.n_active = it.n_active;
+        A.dirs = it.dirs;
+        A.weights = it.weights;
+        A.J = it.J;
+        base += (long long)((it.n_lambda + W - 1) / W) * it.capacity;
+        if ((size_t)A.n_words > max_words) max_words = (size_t)A.n_words;
+    }
+    if (base > 0xffffffffLL) return fail(ctx, DEX_ERR_ARG, "too many work items");
+    P.n_items = base;
+    return DEX_OK;
+}
+
+// Zero every J, then launch the persistent solve with the given work counter.
+static int batch_launch(dex_ctx* ctx, dex::BatchParams& P, const dex_batch_item* atms, int W, int ctas,
+                        size_t max_words, unsigned int* queue, unsigned long long* done_ns,
+                        unsigned long long* start_ns)
+{
+    P.queue = queue;
+    P.done_ns = done_ns;
+    P.start_ns = start_ns;
+    P.status = ctx->status;
+    if (ctas <= 0) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        ctas = 3 * (sms > 0 ? sms : 152);
+    }
+    cudaError_t e = cudaSuccess;
+    for (int a = 0; a < P.n_atm && e == cudaSuccess; ++a)
+        e = cudaMemsetAsync(atms[a].J, 0, sizeof(float) * (size_t)atms[a].n_lambda * atms[a].nx * atms[a].nz,
+                            ctx->stream);
+    if (e == cudaSuccess && done_ns) e = cudaMemsetAsync(done_ns, 0, sizeof(unsigned long long) * P.n_atm, ctx->stream);
+    if (e == cudaSuccess && start_ns) e = cudaMemsetAsync(start_ns, 0xff, sizeof(unsigned long long), ctx->stream);
+    if (e == cudaSuccess) e = dex::launch_batch_solve(ctx->stream, P, ctas, W, max_words);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch_solve launch");
+    return ok(ctx);
+}
+
+int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, int ctas, unsigned int* queue,
+                    unsigned long long* done_ns, unsigned long long* start_ns)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (!queue) return fail(ctx, DEX_ERR_ARG, "queue (device scratch word) required");
+    dex::BatchParams* P = new (std::nothrow) dex::BatchParams();
+    if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    size_t max_words = 0;
+    int r = fill_batch(ctx, n_atm, atms, W, *P, max_words);
+    if (!r) r = bind(ctx);
+    if (!r) r = batch_launch(ctx, *P, atms, W, ctas, max_words, queue, done_ns, start_ns);
+    delete P;
     return r;
 }
 

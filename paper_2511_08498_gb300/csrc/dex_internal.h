@@ -114,6 +114,37 @@ cudaError_t launch_cav_grid_build(cudaStream_t s, int nx, int nz, const CavField
 cudaError_t launch_cav_mips_build(cudaStream_t s, const CavMipParams& P, const CavParams& M);
 cudaError_t launch_solve_cav(cudaStream_t s, const HddaParams& P, const CavParams& M);
 
+int vel_record_floats(int W);
+cudaError_t launch_vel_mips_build(cudaStream_t s, const CavMipParams& P, const CavParams& M);
+cudaError_t launch_solve_velinterp(cudaStream_t s, const HddaParams& P);
+
+struct AtmDesc {
+    int nx, nz, nbx, nbz, n_lambda, chain, n_words, cap_active, n_dir, n_band;
+    float band[4];
+    float i_bc;
+    long long item_base;
+    const float* bricks;
+    const unsigned long long* words;
+    const int* block_offset;
+    const int* active;
+    const int* n_active;
+    const float* dirs;
+    const float* weights;
+    float* J;
+};
+
+struct BatchParams {
+    int n_atm;
+    long long n_items;
+    unsigned int* queue;
+    unsigned long long* done_ns;
+    unsigned long long* start_ns;
+    unsigned int* status;
+    AtmDesc atm[DEX_MAX_BATCH_ATM];
+};
+
+cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, size_t smem_words);
+
 int chain_length(int max_mip);
 cudaError_t launch_voigt(cudaStream_t s, long long n, const float* a, const float* x, float* h);
 cudaError_t launch_synth_static_line(cudaStream_t s, long long n_cells, int n_lambda, const float* chi_c,

@@ -9,15 +9,24 @@ namespace dex {
 
 __host__ __device__ constexpr int level_offset(int m) { return 341 - (341 >> (2 * m)); }
 
+// Geometry of one sparse grid as the traversal needs it.
+struct Geo {
+    int nx, nz, nbx, nbz, chain, cap_active;
+    const float* batch_base;   // bricks of the wavelength batch being solved
+    const int* block_offset;
+    int n_band;                // < 0: no distance limit
+    float band[4];
+};
+
 // Highest level a block first entered at ray parameter t may use: with
 // distance limits, the number of thresholds band[m-1] <= t (Section 4.1: the
 // near field at full resolution, coarser levels only further out).
-__device__ __forceinline__ int distance_cap(const HddaParams& P, float t)
+__device__ __forceinline__ int distance_cap(const Geo& G, float t)
 {
-    if (P.n_band < 0) return 4;
+    if (G.n_band < 0) return 4;
     int m = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) m += (q < P.n_band && P.band[q] <= t) ? 1 : 0;
+    for (int q = 0; q < 4; ++q) m += (q < G.n_band && G.band[q] <= t) ? 1 : 0;
     return m;
 }
 
@@ -30,6 +39,116 @@ __device__ __forceinline__ int block_state(const unsigned long long* words, int 
 // Voxel models: Model::kStride floats per voxel record, Model::kPerBatch whether
 // records differ per wavelength batch, Model::Voxel / load / integrate the
 // per-segment update of the W wavelengths of batch b along propagation (wx, wz).
+//
+// One ray from the centre of cell (i, j) (in active block a0 = (bx0, bz0), whose
+// level is mip0) along d = (dx, dz): accumulates I and T (initialised by the
+// caller) over the traversal; s_words holds the batch's packed block states.
+template <int W, bool COUNT, class Model>
+__device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Params& M, int b, int i, int j,
+                                          int bx0, int bz0, int a0, int mip0, float dx, float dz,
+                                          const unsigned long long* __restrict__ s_words, float* I, float* T,
+                                          unsigned int& nseg, bool& capped)
+{
+    constexpr int REC = Model::kStride;
+    const float* __restrict__ batch_base = G.batch_base;
+    const int cap = 2 * (G.nx + G.nz) + 64;
+    const float ox = (float)i + 0.5f, oz = (float)j + 0.5f;
+    const bool negx = dx < 0.0f, negz = dz < 0.0f;
+    const int sx = negx ? -1 : 1, sz = negz ? -1 : 1;
+    const AxisParam ax = axis_param(dx), az = axis_param(dz);
+    const float Ex = negx ? (float)(-i) - 0.5f : (float)(G.nx - i) - 0.5f;
+    const float Ez = negz ? (float)(-j) - 0.5f : (float)(G.nz - j) - 0.5f;
+    const float t2 = fminf(Ex * ax.ih, Ez * az.ih);
+
+    // tracer state: level, voxel size, block, block-local voxel, far-face plane offsets
+    int mip = mip0, vox = 1 << mip0, side = DEX_BLOCK >> mip0;
+    int bxc = bx0, bzc = bz0;
+    int lx = (i - bx0 * DEX_BLOCK) >> mip, lz = (j - bz0 * DEX_BLOCK) >> mip;
+    float Px = (float)(bx0 * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
+    float Pz = (float)(bz0 * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
+    const float* rp = batch_base + ((size_t)a0 * G.chain + level_offset(mip) + lz * side + lx) * REC;
+    float th_prev = 0.0f, tl_prev = 0.0f;
+    typename Model::Voxel cur;
+
+    for (int it = 0;; ++it) {
+        const float tnx = Px * ax.ih, tnz = Pz * az.ih;
+        const bool on_x = tnx <= tnz;
+        const float th = on_x ? tnx : tnz;
+        const float tl = plane_lo(on_x ? Px : Pz, on_x ? ax : az, th);
+        const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
+        const bool last = th >= t2;
+        const int cur_mip = mip;
+        const float* cur_rp = rp;
+        if (!last) {
+            if (it >= cap) { capped = true; break; }
+            const float fv = (float)vox;
+            bool cross;
+            if (on_x) {
+                lx += sx;
+                Px += negx ? -fv : fv;
+                rp += negx ? -REC : REC;
+                cross = (unsigned)lx >= (unsigned)side;
+            } else {
+                lz += sz;
+                Pz += negz ? -fv : fv;
+                rp += negz ? -side * REC : side * REC;
+                cross = (unsigned)lz >= (unsigned)side;
+            }
+            if (cross) {  // entered another block
+                const int bxn = bxc + (on_x ? sx : 0), bzn = bzc + (on_x ? 0 : sz);
+                if ((unsigned)bxn >= (unsigned)G.nbx || (unsigned)bzn >= (unsigned)G.nbz) {
+                    capped = true;
+                    break;
+                }
+                const int blk = bzn * G.nbx + bxn;
+                const int st = block_state(s_words, blk) - 1;
+                const int mip_new = st < 0 ? -1 : min(st, distance_cap(G, th));
+                if (mip_new == mip) {
+                    if (on_x) lx = negx ? side - 1 : 0;
+                    else lz = negz ? side - 1 : 0;
+                } else {
+                    // MIP-0 cell entered: exact on the stepped axis, from p(t) on the
+                    // other one, clamped to the voxel just left
+                    const int vox_old = vox;
+                    int m0x, m0z;
+                    if (on_x) {
+                        m0x = bxn * DEX_BLOCK + (negx ? DEX_BLOCK - 1 : 0);
+                        const int lo = bzc * DEX_BLOCK + lz * vox_old;
+                        m0z = min(max(__float2int_rd(fmaf(th, dz, oz)), lo), lo + vox_old - 1);
+                    } else {
+                        m0z = bzn * DEX_BLOCK + (negz ? DEX_BLOCK - 1 : 0);
+                        const int lo = bxc * DEX_BLOCK + lx * vox_old;
+                        m0x = min(max(__float2int_rd(fmaf(th, dx, ox)), lo), lo + vox_old - 1);
+                    }
+                    mip = mip_new;
+                    const int shift = mip >= 0 ? mip : 4;
+                    vox = 1 << shift;
+                    side = DEX_BLOCK >> shift;
+                    lx = (m0x - bxn * DEX_BLOCK) >> shift;
+                    lz = (m0z - bzn * DEX_BLOCK) >> shift;
+                    Px = (float)(bxn * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
+                    Pz = (float)(bzn * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
+                }
+                bxc = bxn;
+                bzc = bzn;
+                if (mip >= 0) {
+                    const int a = G.block_offset[blk];
+                    rp = batch_base + ((size_t)a * G.chain + level_offset(mip) + lz * side + lx) * REC;
+                }
+            }
+        }
+        if (cur_mip >= 0) {
+            cur = Model::load(cur_rp);
+            const float nl2 = len * kNegLog2e;
+            Model::integrate(M, cur, b, -dx, -dz, nl2, I, T);
+            if (COUNT) nseg += (th > th_prev);
+        }
+        if (last) break;
+        th_prev = th;
+        tl_prev = tl;
+    }
+}
+
 template <int W, bool COUNT, class Model>
 __global__ void __launch_bounds__(256) k_solve_hdda_t(const HddaParams P, const typename Model::Params M)
 {
@@ -52,116 +171,28 @@ __global__ void __launch_bounds__(256) k_solve_hdda_t(const HddaParams P, const 
         raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
         return;
     }
-    const int mip0 = min(state0, distance_cap(P, 0.0f));
-    constexpr int REC = Model::kStride;
-    const float* __restrict__ batch_base =
-        P.bricks + (Model::kPerBatch ? (size_t)b * P.cap_active * P.chain * REC : (size_t)0);
-    const int cap = 2 * (P.nx + P.nz) + 64;
-    const float ox = (float)i + 0.5f, oz = (float)j + 0.5f;
+    Geo G;
+    G.nx = P.nx;
+    G.nz = P.nz;
+    G.nbx = P.nbx;
+    G.nbz = P.nbz;
+    G.chain = P.chain;
+    G.cap_active = P.cap_active;
+    G.batch_base = P.bricks + (Model::kPerBatch ? (size_t)b * P.cap_active * P.chain * Model::kStride : (size_t)0);
+    G.block_offset = P.block_offset;
+    G.n_band = P.n_band;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) G.band[q] = P.band[q];
+    const int mip0 = min(state0, distance_cap(G, 0.0f));
     unsigned int nseg = 0;
     bool capped = false;
 
     for (int k = 0; k < P.quad.n_dir; ++k) {
         const float dx = P.quad.dx[k], dz = P.quad.dz[k];
-        // a zero component counts as positive: its plane offsets stay positive
-        // and their parameters (offset * inf) are +inf, so that axis never steps
-        const bool negx = dx < 0.0f, negz = dz < 0.0f;
-        const int sx = negx ? -1 : 1, sz = negz ? -1 : 1;
-        const AxisParam ax = axis_param(dx), az = axis_param(dz);
-        const float Ex = negx ? (float)(-i) - 0.5f : (float)(P.nx - i) - 0.5f;
-        const float Ez = negz ? (float)(-j) - 0.5f : (float)(P.nz - j) - 0.5f;
-        const float t2 = fminf(Ex * ax.ih, Ez * az.ih);
-
-        // tracer state: level, voxel size, block, block-local voxel, far-face plane offsets
-        int mip = mip0, vox = 1 << mip0, side = DEX_BLOCK >> mip0;
-        int bxc = bx0, bzc = bz0;
-        int lx = (i - bx0 * DEX_BLOCK) >> mip, lz = (j - bz0 * DEX_BLOCK) >> mip;
-        float Px = (float)(bx0 * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
-        float Pz = (float)(bz0 * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
-        const float* rp = batch_base + ((size_t)a0 * P.chain + level_offset(mip) + lz * side + lx) * REC;
-        float th_prev = 0.0f, tl_prev = 0.0f;
         float I[W], T[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
-        typename Model::Voxel cur;
-
-        for (int it = 0;; ++it) {
-            const float tnx = Px * ax.ih, tnz = Pz * az.ih;
-            const bool on_x = tnx <= tnz;
-            const float th = on_x ? tnx : tnz;
-            const float tl = plane_lo(on_x ? Px : Pz, on_x ? ax : az, th);
-            const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
-            const bool last = th >= t2;
-            const int cur_mip = mip;
-            const float* cur_rp = rp;
-            if (!last) {
-                if (it >= cap) { capped = true; break; }
-                const float fv = (float)vox;
-                bool cross;
-                if (on_x) {
-                    lx += sx;
-                    Px += negx ? -fv : fv;
-                    rp += negx ? -REC : REC;
-                    cross = (unsigned)lx >= (unsigned)side;
-                } else {
-                    lz += sz;
-                    Pz += negz ? -fv : fv;
-                    rp += negz ? -side * REC : side * REC;
-                    cross = (unsigned)lz >= (unsigned)side;
-                }
-                if (cross) {  // entered another block
-                    const int bxn = bxc + (on_x ? sx : 0), bzn = bzc + (on_x ? 0 : sz);
-                    if ((unsigned)bxn >= (unsigned)P.nbx || (unsigned)bzn >= (unsigned)P.nbz) {
-                        capped = true;
-                        break;
-                    }
-                    const int blk = bzn * P.nbx + bxn;
-                    const int st = block_state(s_words, blk) - 1;
-                    const int mip_new = st < 0 ? -1 : min(st, distance_cap(P, th));
-                    if (mip_new == mip) {
-                        if (on_x) lx = negx ? side - 1 : 0;
-                        else lz = negz ? side - 1 : 0;
-                    } else {
-                        // MIP-0 cell entered: exact on the stepped axis, from p(t) on the
-                        // other one, clamped to the voxel just left
-                        const int vox_old = vox;
-                        int m0x, m0z;
-                        if (on_x) {
-                            m0x = bxn * DEX_BLOCK + (negx ? DEX_BLOCK - 1 : 0);
-                            const int lo = bzc * DEX_BLOCK + lz * vox_old;
-                            m0z = min(max(__float2int_rd(fmaf(th, dz, oz)), lo), lo + vox_old - 1);
-                        } else {
-                            m0z = bzn * DEX_BLOCK + (negz ? DEX_BLOCK - 1 : 0);
-                            const int lo = bxc * DEX_BLOCK + lx * vox_old;
-                            m0x = min(max(__float2int_rd(fmaf(th, dx, ox)), lo), lo + vox_old - 1);
-                        }
-                        mip = mip_new;
-                        const int shift = mip >= 0 ? mip : 4;
-                        vox = 1 << shift;
-                        side = DEX_BLOCK >> shift;
-                        lx = (m0x - bxn * DEX_BLOCK) >> shift;
-                        lz = (m0z - bzn * DEX_BLOCK) >> shift;
-                        Px = (float)(bxn * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
-                        Pz = (float)(bzn * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
-                    }
-                    bxc = bxn;
-                    bzc = bzn;
-                    if (mip >= 0) {
-                        const int a = P.block_offset[blk];
-                        rp = batch_base + ((size_t)a * P.chain + level_offset(mip) + lz * side + lx) * REC;
-                    }
-                }
-            }
-            if (cur_mip >= 0) {
-                cur = Model::load(cur_rp);
-                const float nl2 = len * kNegLog2e;
-                Model::integrate(M, cur, b, -dx, -dz, nl2, I, T);
-                if (COUNT) nseg += (th > th_prev);
-            }
-            if (last) break;
-            th_prev = th;
-            tl_prev = tl;
-        }
+        trace_ray<W, COUNT, Model>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz, s_words, I, T, nseg, capped);
         const float wk = P.quad.w[k];
 #pragma unroll
         for (int w = 0; w < W; ++w) {

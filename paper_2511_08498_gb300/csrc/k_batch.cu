@@ -1,0 +1,153 @@
+// Many independent atmospheres in one persistent launch.
+//
+// Work items are (atmosphere, wavelength batch, active block), numbered
+// atmosphere by atmosphere (item_base[a] + batch * capacity_a + rank).  A fixed
+// grid of CTAs pulls items from a device counter (the queue) until it runs dry;
+// each item is the same 256-probe block solve as k_solve_hdda_t (shared
+// trace_ray).  Consecutive items mostly share an atmosphere and batch, so the
+// staged block states and quadrature are reused, and the L2 working set stays
+// one atmosphere batch wide.  Per-atmosphere completion times (globaltimer, ns)
+// are recorded when requested.
+#include "hdda.cuh"
+
+namespace dex {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int W>
+struct StaticRec {
+    static constexpr int kStride = 2 * W;
+    static constexpr bool kPerBatch = true;
+    struct Params {
+        int unused;
+    };
+    using Voxel = Record<W>;
+    __device__ __forceinline__ static Voxel load(const float* p) { return load_record<W>(p); }
+    __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
+                                                     float* I, float* T)
+    {
+#pragma unroll
+        for (int w = 0; w < W; ++w) segment(v.S[w], v.chi[w], nl2, I[w], T[w]);
+    }
+};
+
+template <int W>
+__global__ void __launch_bounds__(256) k_batch_solve(const BatchParams P)
+{
+    extern __shared__ unsigned long long s_words[];
+    __shared__ float s_J[W][256];
+    __shared__ float s_dx[DEX_MAX_DIRS], s_dz[DEX_MAX_DIRS], s_w[DEX_MAX_DIRS];
+    __shared__ unsigned int s_item;
+    const int tid = threadIdx.x;
+    int cur_atm = -1, cur_batch = -1;
+    unsigned int nseg_unused = 0;
+    bool capped = false;
+    if (P.start_ns != nullptr && tid == 0) atomicMin(P.start_ns, global_ns());
+
+    for (;;) {
+        __syncthreads();  // every thread is done with the previous item's shared data
+        if (tid == 0) s_item = atomicAdd(P.queue, 1u);
+        __syncthreads();
+        const unsigned int item = s_item;
+        if ((long long)item >= P.n_items) break;
+        int a = 0;
+        while (a + 1 < P.n_atm && (long long)item >= P.atm[a + 1].item_base) ++a;
+        const AtmDesc& A = P.atm[a];
+        const long long local = (long long)item - A.item_base;
+        const int b = (int)(local / A.cap_active), r = (int)(local % A.cap_active);
+        if (r >= *A.n_active) continue;
+        if (a != cur_atm || b != cur_batch) {
+            for (int q = tid; q < A.n_words; q += blockDim.x) s_words[q] = A.words[(size_t)b * A.n_words + q];
+            if (a != cur_atm)
+                for (int q = tid; q < A.n_dir; q += blockDim.x) {
+                    s_dx[q] = A.dirs[2 * q];
+                    s_dz[q] = A.dirs[2 * q + 1];
+                    s_w[q] = A.weights[q];
+                }
+            cur_atm = a;
+            cur_batch = b;
+        }
+#pragma unroll
+        for (int w = 0; w < W; ++w) s_J[w][tid] = 0.0f;
+        __syncthreads();
+
+        const int blk0 = A.active[r];
+        const int bx0 = blk0 % A.nbx, bz0 = blk0 / A.nbx;
+        const int i = bx0 * DEX_BLOCK + (tid & 15), j = bz0 * DEX_BLOCK + (tid >> 4);
+        const int state0 = block_state(s_words, blk0) - 1;
+        if (state0 < 0) {
+            capped = true;
+            continue;
+        }
+        Geo G;
+        G.nx = A.nx;
+        G.nz = A.nz;
+        G.nbx = A.nbx;
+        G.nbz = A.nbz;
+        G.chain = A.chain;
+        G.cap_active = A.cap_active;
+        G.batch_base = A.bricks + (size_t)b * A.cap_active * A.chain * (2 * W);
+        G.block_offset = A.block_offset;
+        G.n_band = A.n_band;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) G.band[q] = A.band[q];
+        const int mip0 = min(state0, distance_cap(G, 0.0f));
+        typename StaticRec<W>::Params M{};
+        for (int k = 0; k < A.n_dir; ++k) {
+            float I[W], T[W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
+            trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k], s_words, I, T,
+                                               nseg_unused, capped);
+            const float wk = s_w[k];
+#pragma unroll
+            for (int w = 0; w < W; ++w) s_J[w][tid] = fmaf(wk, fmaf(T[w], A.i_bc, I[w]), s_J[w][tid]);
+        }
+        const long long n_cells = (long long)A.nx * A.nz;
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            const int l = b * W + w;
+            if (l < A.n_lambda) A.J[(size_t)l * n_cells + (size_t)j * A.nx + i] = s_J[w][tid];
+        }
+        if (P.done_ns != nullptr) {
+            __syncthreads();
+            if (tid == 0) atomicMax(P.done_ns + a, global_ns());
+        }
+    }
+    if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
+}
+
+}  // namespace
+
+cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, size_t smem_words)
+{
+    cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess || P.n_items == 0) return e;
+    const size_t smem = sizeof(unsigned long long) * smem_words;
+    switch (W) {
+#define DEX_LAUNCH(WW)                                                                                  \
+    case WW:                                                                                            \
+        if (smem > 16 * 1024)                                                                           \
+            e = cudaFuncSetAttribute(k_batch_solve<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                     (int)smem);                                                        \
+        if (e == cudaSuccess) k_batch_solve<WW><<<(unsigned)ctas, 256, smem, s>>>(P);                   \
+        break;
+        DEX_LAUNCH(1)
+        DEX_LAUNCH(2)
+        DEX_LAUNCH(4)
+        DEX_LAUNCH(8)
+#undef DEX_LAUNCH
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace dex

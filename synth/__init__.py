@@ -18,4 +18,5 @@ from .atmospheres import (  # noqa: F401
     gaussian_field,
     random_medium,
     dynamic_line_atmosphere,
+    batch_specs,
 )

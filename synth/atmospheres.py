@@ -257,3 +257,25 @@ def dynamic_line_atmosphere(nx: int = 2048, nz: int = 1024, block: int = 16, n_l
         "dv": dv.astype(np.float32), "lambda0_nm": float(lambda0_nm), "c_kms": C_KMS,
         "empty_block_frac": frac, "block": block,
     }
+
+
+def batch_specs(n_atm: int = 24, seed: int = SEED_BASE + 5, sizes=((256, 256), (2048, 1024)),
+                n_lambda=(16, 96), n_dir=(32, 128), empty=(0.1, 0.7), scale: float = 1.0):
+    """Seeded list of independent atmosphere specs for the batched workload.
+
+    Side lengths are drawn log-uniformly between the two corner sizes (multiples of
+    64, times ``scale``), wavelength counts and direction counts uniformly in
+    multiples of 8, empty-block fractions uniformly.  Each spec carries its own seed
+    for ``sparse_line_atmosphere``.
+    """
+    rng = np.random.default_rng(seed)
+    (x0, z0), (x1, z1) = sizes
+    out = []
+    for a in range(n_atm):
+        nx = int(round(np.exp(rng.uniform(np.log(x0), np.log(x1))) * scale / 64)) * 64
+        nz = int(round(np.exp(rng.uniform(np.log(z0), np.log(z1))) * scale / 64)) * 64
+        out.append({"nx": max(nx, 64), "nz": max(nz, 64),
+                    "n_lambda": int(rng.integers(n_lambda[0] // 8, n_lambda[1] // 8 + 1)) * 8,
+                    "n_dir": int(rng.integers(n_dir[0] // 8, n_dir[1] // 8 + 1)) * 8,
+                    "empty_frac": float(rng.uniform(*empty)), "seed": int(seed * 100 + a)})
+    return out

@@ -1,0 +1,52 @@
+"""Batched persistent solve: bit-identical to per-atmosphere solves (same traversal,
+same summation order), and to the oracle through them."""
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def build_atmospheres(ctx, specs, W=8, iod=1.0, band=(6.0, 24.0, 96.0)):
+    from paper_2511_08498_gb300 import api
+    out = []
+    for sp in specs:
+        m = synth.sparse_line_atmosphere(sp["nx"], sp["nz"], n_lambda=sp["n_lambda"], empty_frac=sp["empty_frac"],
+                                         seed=sp["seed"])
+        t = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda()
+             for k in ("chi_c", "s_c", "s_l", "ratio", "dld", "dlam")}
+        eta, chi = api.synth_static_line(ctx, t["chi_c"], t["s_c"], t["s_l"], t["ratio"], t["dld"], t["dlam"])
+        grid = api.grid_build(ctx, sp["nx"], sp["nz"], eta, chi)
+        mp = api.mips_build(ctx, grid, eta, chi, W, 3, iod, iod, 0.25)
+        dirs, w = synth.directions(sp["n_dir"])
+        out.append(dict(grid=grid, mips=mp, dirs=dirs, w=w, dirs_dev=torch.from_numpy(dirs).cuda(),
+                        w_dev=torch.from_numpy(w).cuda(), band=list(band),
+                        J=torch.empty((sp["n_lambda"], sp["nx"] * sp["nz"]), device="cuda")))
+    return out
+
+
+SPECS = [dict(nx=64, nz=48, n_lambda=16, n_dir=8, empty_frac=0.3, seed=11),
+         dict(nx=96, nz=64, n_lambda=24, n_dir=12, empty_frac=0.5, seed=12),
+         dict(nx=48, nz=96, n_lambda=8, n_dir=16, empty_frac=0.1, seed=13),
+         dict(nx=128, nz=32, n_lambda=8, n_dir=4, empty_frac=0.7, seed=14)]
+
+
+@pytest.mark.parametrize("ctas", [0, 1, 7])
+def test_batch_equals_per_atmosphere(ctas):
+    from paper_2511_08498_gb300 import api
+    ctx = api.Context(0)
+    atms = build_atmospheres(ctx, SPECS)
+    refs = []
+    for a in atms:
+        J, _, _ = api.formal_solve_hdda(ctx, a["grid"], a["mips"], a["dirs"], a["w"], band=a["band"])
+        refs.append(J.clone())
+    items = [api.batch_item(a["grid"], a["mips"], a["dirs_dev"], a["w_dev"], a["J"], band=a["band"]) for a in atms]
+    done, start = api.batch_solve(ctx, items, 8, ctas=ctas, timing=True)
+    ctx.check()
+    for a, r in zip(atms, refs):
+        assert torch.equal(a["J"], r)
+    d = done.cpu().numpy()
+    assert (d > 0).all() and (d >= int(start.item())).all()
