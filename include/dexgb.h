@@ -424,6 +424,37 @@ typedef struct {
 int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, int ctas, unsigned int* queue,
                     unsigned long long* done_ns, unsigned long long* start_ns);
 
+/*
+ * Allocation-free variant of dex_batch_solve (the paper has no counterpart:
+ * this is a deployment convenience of this library).
+ *
+ * For callers that cannot allocate device memory when they solve: a host
+ * application that owns every byte of the device through its own pool, or a
+ * time-critical loop where a cudaMalloc -- which may synchronise the device --
+ * is not acceptable.  Such a caller has no place to put the one scratch word
+ * (the work counter) that dex_batch_solve takes as `queue`.  This entry point
+ * keeps that scratch in a statically sized device array inside the library
+ * instead: DEX_NOALLOC_SCRATCH_WORDS words (256 bytes), held on every GPU that
+ * loads the library until the process exits.  The caller still provides all
+ * inputs and outputs (descriptors, J, optional done_ns / start_ns).
+ *
+ * - It calls no cudaMalloc/cudaFree and makes no other allocation, on the device
+ *   or the host; the counter is reset by the call before the launch.
+ * - The first call on a device looks up the device address of the array (with
+ *   that device current) and caches it; make that first call before any stream
+ *   capture.
+ * - Every call shares the same array: calls that overlap on the GPU (different
+ *   streams, or different contexts on one device) race on the counter.
+ *   Serialise them.
+ * - Limits as dex_batch_solve: n_atm <= DEX_MAX_BATCH_ATM and at most 2^32 - 1
+ *   work items in total; larger requests are rejected with DEX_ERR_ARG.
+ * Arguments and results otherwise as dex_batch_solve (no `queue`).
+ */
+#define DEX_NOALLOC_SCRATCH_WORDS 64
+
+int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, int ctas,
+                            unsigned long long* done_ns, unsigned long long* start_ns);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ PROTOTYPES = {
                                            c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float,
                                            c_void_p, c_void_p, c_void_p]),
     "dex_batch_solve": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "dex_batch_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]),
 }
 
 

@@ -549,3 +549,13 @@ def batch_solve(ctx: Context, items, W: int, ctas: int = 0, queue: torch.Tensor 
     start = torch.zeros(1, dtype=torch.int64, device=dev) if timing else None
     ctx._rc(lib().dex_batch_solve(ctx.handle, n, arr, W, int(ctas), _ptr(queue), _ptr(done), _ptr(start)))
     return done, start
+
+
+def batch_solve_noalloc(ctx: Context, items, W: int, ctas: int = 0, done_ns: torch.Tensor | None = None,
+                        start_ns: torch.Tensor | None = None):
+    """``dex_batch_solve_noalloc``: the batched solve for callers that cannot allocate
+    device memory when they solve (the work counter lives in the library's static
+    scratch).  Outputs are the caller's; pass preallocated ``done_ns`` [n] and
+    ``start_ns`` [1] int64 tensors to get completion times."""
+    arr = (BatchItem * len(items))(*items)
+    ctx._rc(lib().dex_batch_solve_noalloc(ctx.handle, len(items), arr, W, int(ctas), _ptr(done_ns), _ptr(start_ns)))

@@ -823,4 +823,18 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
     return r;
 }
 
+int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, int ctas,
+                            unsigned long long* done_ns, unsigned long long* start_ns)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    dex::BatchParams P{};  // on the stack: this call makes no allocation at all
+    size_t max_words = 0;
+    if (int r = fill_batch(ctx, n_atm, atms, W, P, max_words)) return r;
+    if (int r = bind(ctx)) return r;
+    unsigned int* scratch = nullptr;
+    cudaError_t e = dex::noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "static scratch address");
+    return batch_launch(ctx, P, atms, W, ctas, max_words, scratch, done_ns, start_ns);
+}
+
 }  // extern "C"

@@ -144,6 +144,7 @@ struct BatchParams {
 };
 
 cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, size_t smem_words);
+cudaError_t noalloc_scratch(unsigned int** out);
 
 int chain_length(int max_mip);
 cudaError_t launch_voigt(cudaStream_t s, long long n, const float* a, const float* x, float* h);

@@ -8,11 +8,19 @@
 // staged block states and quadrature are reused, and the L2 working set stays
 // one atmosphere batch wide.  Per-atmosphere completion times (globaltimer, ns)
 // are recorded when requested.
+#include <mutex>
+
 #include "hdda.cuh"
 
 namespace dex {
 
 namespace {
+
+// Scratch of the allocation-free entry point (dex_batch_solve_noalloc): a
+// statically sized device array, present on every GPU that loads the library
+// until the process exits.  Word 0 is the work counter.  Calls that overlap on
+// the GPU share it and race.
+static __device__ __align__(256) unsigned int g_noalloc_scratch[DEX_NOALLOC_SCRATCH_WORDS];
 
 __device__ __forceinline__ unsigned long long global_ns()
 {
@@ -125,6 +133,28 @@ __global__ void __launch_bounds__(256) k_batch_solve(const BatchParams P)
 }
 
 }  // namespace
+
+// Device address of the static scratch array on the current device, looked up
+// once per device (with that device current) and cached.  The array's host-side
+// name is not a device address, so kernels must be given this pointer.
+cudaError_t noalloc_scratch(unsigned int** out)
+{
+    static std::mutex mu;
+    static unsigned int* ptr[256] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (ptr[dev] == nullptr) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        ptr[dev] = static_cast<unsigned int*>(p);
+    }
+    *out = ptr[dev];
+    return cudaSuccess;
+}
 
 cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, size_t smem_words)
 {
