@@ -46,9 +46,11 @@ BAND = [6.0, 24.0, 96.0]
 WORKLOAD = (f"sparse static-line atmosphere {NX}x{NZ}, 16^2 blocks, 40% empty, {N_LAMBDA} wavelengths, "
             f"{N_DIR} directions, VLM mip 0-{MAX_MIP}, IoD threshold {THR:g}, level distance limits "
             f"{BAND}, HDDA, FP32")
-# accelerated variants reported beside the timed step: (name, IoD threshold, distance limits)
-VARIANTS = [("strict_iod_1e-3", THR_STRICT, BAND), ("paper_iod_1", 1.0, BAND),
-            ("unlimited_vlm", 1e30, BAND), ("no_distance_limit_iod_1e-2", THR, None)]
+# accelerated variants reported beside the timed step:
+# (name, IoD threshold, distance limits, brick storage 0 float32 / 1 bfloat16 / 2 float16)
+VARIANTS = [("strict_iod_1e-3", THR_STRICT, BAND, 0), ("paper_iod_1", 1.0, BAND, 0),
+            ("unlimited_vlm", 1e30, BAND, 0), ("no_distance_limit_iod_1e-2", THR, None, 0),
+            ("bf16_bricks", THR, BAND, 1), ("f16_bricks", THR, BAND, 2)]
 # SM count x SFU ex2 results per clock per SM x max SM clock: each segment-wavelength
 # update needs one exponential, so this bounds the updates per second
 SFU_PER_SM_CLK = 16
@@ -164,6 +166,7 @@ class Workload:
         self.J = torch.empty_like(self.eta)
         self.grid = None
         self.mips = None
+        self.mips_by_storage = {}
         self.launches_per_step = 5  # synth, block flags, block layout, mips build, hdda solve
 
     def synth(self):
@@ -171,12 +174,13 @@ class Workload:
         self.api.synth_static_line(self.ctx, d["chi_c"], d["s_c"], d["s_l"], d["ratio"], d["dld"], d["dlam"],
                                    eta=self.eta, chi=self.chi)
 
-    def step(self, thr=THR, band=BAND, ev=None, count=False):
+    def step(self, thr=THR, band=BAND, ev=None, count=False, storage=0):
         api = self.api
         self.synth()
         self.grid = api.grid_build(self.ctx, NX, NZ, self.eta, self.chi, out=self.grid)
         self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, W, MAX_MIP, thr, thr, CHI_DS_MIN,
-                                   log_mean=False, out=self.mips)
+                                   log_mean=False, out=self.mips_by_storage.get(storage), storage=storage)
+        self.mips_by_storage[storage] = self.mips
         if ev is not None:
             ev[0].record()
         _, _, seg = api.formal_solve_hdda(self.ctx, self.grid, self.mips, self.dirs, self.w, J=self.J,
@@ -306,13 +310,14 @@ def native(args):
 
     # accelerated variants, same protocol
     variants = {}
-    for name, thr, band in VARIANTS:
-        seg_v = wl.step(thr=thr, band=band, count=True)
+    for name, thr, band, storage in VARIANTS:
+        seg_v = wl.step(thr=thr, band=band, count=True, storage=storage)
         J_v = wl.J[:, probes.long()].double()
-        vt, _ = time_steps(lambda ev: wl.step(thr=thr, band=band, ev=ev), max(2, min(args.steps, 3)), 1, torch,
-                           flush)
+        vt, vk = time_steps(lambda ev: wl.step(thr=thr, band=band, ev=ev, storage=storage),
+                            max(2, min(args.steps, 3)), 1, torch, flush)
         v_s = sum(vt) / 1e3 / len(vt)
-        variants[name] = {"iod_threshold": thr, "distance_limits": band, "ms_per_step": v_s * 1e3,
+        variants[name] = {"iod_threshold": thr, "distance_limits": band, "storage": ["f32", "bf16", "f16"][storage],
+                          "ms_per_step": v_s * 1e3, "hdda_ms": sum(vk) / len(vk),
                           "value": dense_seg_lambda / v_s, "speedup_vs_plain": plain_s / v_s,
                           "executed_fraction": int(seg_v.item()) * W / dense_seg_lambda,
                           "j_err_pct_vs_plain": err_pct(J_v)}

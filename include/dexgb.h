@@ -174,8 +174,17 @@ size_t dex_state_words(int nx, int nz);
 /* Voxel records of one active block's MIP chain, levels 0..max_mip: sum (16 >> m)^2. */
 int dex_chain_voxels(int max_mip);
 
-/* Floats of the brick array: n_batch * capacity * dex_chain_voxels(max_mip) * 2W. */
-size_t dex_brick_floats(int capacity, int n_lambda, int W, int max_mip);
+/* Record storage formats of the static bricks (accumulation along rays is float32 in all):
+ *   DEX_STORE_F32  : S[W], chi[W] float32                       (2W floats per record)
+ *   DEX_STORE_BF16 : S[W], chi[W] bfloat16, round to nearest    (W floats; W = 4 or 8)
+ *   DEX_STORE_F16  : float32 max S, max chi, 2 pad words, then S / max S and chi / max chi
+ *                    as float16, round to nearest (4 + W floats; W = 4 or 8).  Values
+ *                    below 2^-14 of their record's maximum lose precision (subnormals)
+ *                    and below 2^-24 of it become 0. */
+enum { DEX_STORE_F32 = 0, DEX_STORE_BF16 = 1, DEX_STORE_F16 = 2 };
+
+/* Floats of the brick array: n_batch * capacity * dex_chain_voxels(max_mip) * record floats. */
+size_t dex_brick_floats(int capacity, int n_lambda, int W, int max_mip, int storage);
 
 /* Variance-limited mipmapping parameters (Section 2.2, Section 4.1). */
 typedef struct {
@@ -184,6 +193,7 @@ typedef struct {
     float chi_ds_min;  /* always average where the largest child chi * Ds is below this (0.25) */
     int max_mip;       /* highest level, 0..4 (0: sparse skipping only)                   */
     int log_mean;      /* 1: log-space (geometric) mean of the children; 0: box filter     */
+    int storage;       /* DEX_STORE_F32 / _BF16 / _F16 record format of the bricks         */
 } dex_vlm_params;
 
 /*
@@ -193,7 +203,8 @@ typedef struct {
  *                     on n_active (grid size of the launch; bricks are sized by it)
  *   params            host pointer
  *   level_cap         device [nbz * nbx] per-block upper bound on the level, or NULL
- *   bricks            device [n_batch][capacity][chain][2W] output records:
+ *   bricks            device [n_batch][capacity][chain][record] output records (format
+ *                     params->storage):
  *                     level m of a block starts at record sum_{k<m} (16 >> k)^2 and
  *                     is row-major over its (16 >> m)^2 voxels
  *   state_words       device [n_batch][dex_state_words] output (zeroed by the call):
@@ -212,6 +223,7 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
  * every active block, traversed with a hierarchical DDA that crosses empty
  * blocks in one step and steps at each block's selected MIP level.
  *   bricks, state_words, block_offset, active, n_active, capacity: from the calls above
+ *   storage   the record format the bricks were built with (DEX_STORE_*)
  *   n_band, band  host [n_band] (n_band <= 4) non-decreasing distances, or band = NULL
  *       for no limit: a block first entered at ray parameter t is sampled at level
  *       min(selected level, #{m : band[m-1] <= t}), the long-characteristics form of
@@ -221,7 +233,8 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
  *   I   device [n_lambda][n_dir][nz][nx] output or NULL (zeroed by the call)
  *   seg_count  device uint64 accumulator or NULL: adds the voxel segments integrated
  */
-int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
+int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, int storage,
+                          const float* bricks,
                           const unsigned long long* state_words, const int* block_offset, const int* active,
                           const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
                           int n_band, const float* band, float i_bc, float* J, float* I,

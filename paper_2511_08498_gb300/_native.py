@@ -36,10 +36,10 @@ PROTOTYPES = {
     "dex_grid_build": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dex_state_words": (c_size_t, [c_int, c_int]),
     "dex_chain_voxels": (c_int, [c_int]),
-    "dex_brick_floats": (c_size_t, [c_int, c_int, c_int, c_int]),
+    "dex_brick_floats": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
     "dex_mips_build": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
                                c_void_p, c_void_p, c_void_p, c_void_p]),
-    "dex_formal_solve_hdda": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
+    "dex_formal_solve_hdda": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                       c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float, c_void_p,
                                       c_void_p, c_void_p]),
     "dex_lte_populations": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),

@@ -130,7 +130,10 @@ STATES_PER_WORD = 21
 class VlmParams(ctypes.Structure):
     """``dex_vlm_params``: variance-limited mipmapping thresholds (Section 2.2)."""
     _fields_ = [("iod_eta", ctypes.c_float), ("iod_chi", ctypes.c_float), ("chi_ds_min", ctypes.c_float),
-                ("max_mip", ctypes.c_int), ("log_mean", ctypes.c_int)]
+                ("max_mip", ctypes.c_int), ("log_mean", ctypes.c_int), ("storage", ctypes.c_int)]
+
+
+STORE_F32, STORE_BF16, STORE_F16 = 0, 1, 2
 
 
 class SparseGrid:
@@ -155,9 +158,10 @@ class SparseGrid:
 class Mips:
     """MIP chain bricks and packed block states of every wavelength batch."""
 
-    def __init__(self, bricks, words, W, max_mip, n_lambda, capacity):
+    def __init__(self, bricks, words, W, max_mip, n_lambda, capacity, storage=0):
         self.bricks, self.words = bricks, words
         self.W, self.max_mip, self.n_lambda, self.capacity = W, max_mip, n_lambda, capacity
+        self.storage = storage
 
 
 def synth_static_line(ctx: Context, chi_c, s_c, s_l, ratio, dld, dlam, eta=None, chi=None):
@@ -196,17 +200,20 @@ def chain_voxels(max_mip: int) -> int:
 
 def mips_build(ctx: Context, grid: SparseGrid, eta, chi, W: int, max_mip: int, iod_eta: float, iod_chi: float,
                chi_ds_min: float = 0.25, log_mean: bool = False, level_cap: torch.Tensor | None = None,
-               capacity: int | None = None, out: Mips | None = None):
-    """MIP chains + VLM block levels of every wavelength batch (``dex_mips_build``)."""
+               capacity: int | None = None, out: Mips | None = None, storage: int = STORE_F32):
+    """MIP chains + VLM block levels of every wavelength batch (``dex_mips_build``).
+
+    ``storage``: record format of the bricks (STORE_F32, STORE_BF16, STORE_F16)."""
     n_lambda = eta.shape[0]
     cap = grid.n_blocks if capacity is None else int(capacity)
     n_batch = -(-n_lambda // W)
     if out is None:
-        nf = int(lib().dex_brick_floats(cap, n_lambda, W, max_mip))
-        bricks = torch.empty(max(nf, 1), dtype=torch.float32, device=eta.device)
+        nf = int(lib().dex_brick_floats(cap, n_lambda, W, max_mip, storage))
+        bricks = torch.empty(max(nf, 4), dtype=torch.float32, device=eta.device)
         words = torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=eta.device)
-        out = Mips(bricks, words, W, max_mip, n_lambda, cap)
-    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 1 if log_mean else 0)
+        out = Mips(bricks, words, W, max_mip, n_lambda, cap, storage)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 1 if log_mean else 0,
+                  int(out.storage))
     ctx._rc(lib().dex_mips_build(ctx.handle, grid.nx, grid.nz, n_lambda, W, _ptr(eta), _ptr(chi), _ptr(grid.active),
                                  _ptr(grid.n_active_dev), cap, ctypes.byref(p), _ptr(level_cap), _ptr(out.bricks),
                                  _ptr(out.words)))
@@ -234,9 +241,9 @@ def formal_solve_hdda(ctx: Context, grid: SparseGrid, mips: Mips, dirs, weights,
     fp = ctypes.POINTER(ctypes.c_float)
     b = None if band is None else _host_f32(band).reshape(-1)
     ctx._rc(lib().dex_formal_solve_hdda(
-        ctx.handle, grid.nx, grid.nz, mips.n_lambda, mips.W, mips.max_mip, _ptr(mips.bricks), _ptr(mips.words),
-        _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev), mips.capacity, d.shape[0],
-        d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
+        ctx.handle, grid.nx, grid.nz, mips.n_lambda, mips.W, mips.max_mip, int(mips.storage), _ptr(mips.bricks),
+        _ptr(mips.words), _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev), mips.capacity,
+        d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
         None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
     return J, I, seg
 
@@ -331,13 +338,14 @@ def se_solve(ctx: Context, atom: Atom, T, ne, nh, jbar, out=None):
 
 def lambda_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, nz: int, dirs, weights,
                      n_iter: int, accelerated: bool = False, W: int = 8, max_mip: int = 3, iod: float = 1e-2,
-                     chi_ds_min: float = 0.25, band=None, pops=None):
+                     chi_ds_min: float = 0.25, band=None, pops=None, storage: int = STORE_F32):
     """Fixed-length Lambda iteration: [eta, chi -> formal solution -> Jbar -> SE] x n_iter.
 
     Every step is a library call; this function only sequences them.  The plain
     variant solves at full resolution from every cell of every non-empty block
     (``dex_formal_solve_dense`` over that probe list); the accelerated one builds
-    the MIP chains and runs the HDDA solve.  Returns the float64 populations.
+    the MIP chains (records in the ``storage`` format) and runs the HDDA solve.
+    Returns the float64 populations.
     """
     n = nx * nz
     L = int(np.asarray(lam_nm).size)
@@ -352,7 +360,7 @@ def lambda_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, 
         atom_eta_chi(ctx, atom, lam_nm, tag, T, ne, pops, eta, chi)
         grid = grid_build(ctx, nx, nz, eta, chi, out=grid)
         if accelerated:
-            mips = mips_build(ctx, grid, eta, chi, W, max_mip, iod, iod, chi_ds_min, out=mips)
+            mips = mips_build(ctx, grid, eta, chi, W, max_mip, iod, iod, chi_ds_min, out=mips, storage=storage)
             formal_solve_hdda(ctx, grid, mips, dirs, weights, J=J, band=band)
         else:
             if probes is None:
@@ -424,7 +432,7 @@ def cav_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: floa
                       torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=dev),
                       W, max_mip, dvh, c_kms, cap)
     f = CavFields.from_tensors(fields)
-    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0, STORE_F32)
     fp = ctypes.POINTER(ctypes.c_float)
     ctx._rc(lib().dex_cav_mips_build(ctx.handle, grid.nx, grid.nz, ctypes.byref(f), dvh.size, W,
                                      dvh.ctypes.data_as(fp), float(c_kms), _ptr(grid.active), _ptr(grid.n_active_dev),
@@ -472,7 +480,7 @@ def vel_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: floa
                       torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=dev),
                       W, max_mip, dvh, c_kms, cap)
     f = CavFields.from_tensors(fields)
-    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0, STORE_F32)
     fp = ctypes.POINTER(ctypes.c_float)
     ctx._rc(lib().dex_vel_mips_build(ctx.handle, grid.nx, grid.nz, ctypes.byref(f), dvh.size, W,
                                      dvh.ctypes.data_as(fp), float(c_kms), _ptr(grid.active), _ptr(grid.n_active_dev),
@@ -519,6 +527,8 @@ class BatchItem(ctypes.Structure):
 
 def batch_item(grid: SparseGrid, mips: Mips, dirs_dev: torch.Tensor, weights_dev: torch.Tensor, J: torch.Tensor,
                band=None, i_bc: float = 0.0) -> BatchItem:
+    if getattr(mips, "storage", STORE_F32) != STORE_F32:
+        raise ValueError("the batched solve reads float32 bricks")
     it = BatchItem()
     it.nx, it.nz, it.n_lambda, it.max_mip, it.capacity = grid.nx, grid.nz, mips.n_lambda, mips.max_mip, mips.capacity
     it.bricks, it.state_words = mips.bricks.data_ptr(), mips.words.data_ptr()

@@ -310,11 +310,17 @@ int dex_chain_voxels(int max_mip)
     return dex::chain_length(max_mip);
 }
 
-size_t dex_brick_floats(int capacity, int n_lambda, int W, int max_mip)
+static bool valid_storage(int W, int storage)
 {
-    if (capacity < 0 || n_lambda < 0 || !valid_W(W) || max_mip < 0 || max_mip > 4) return 0;
+    return storage == DEX_STORE_F32 || ((storage == DEX_STORE_BF16 || storage == DEX_STORE_F16) && (W == 4 || W == 8));
+}
+
+size_t dex_brick_floats(int capacity, int n_lambda, int W, int max_mip, int storage)
+{
+    if (capacity < 0 || n_lambda < 0 || !valid_W(W) || max_mip < 0 || max_mip > 4 || !valid_storage(W, storage))
+        return 0;
     const size_t n_batch = (size_t)((n_lambda + W - 1) / W);
-    return n_batch * (size_t)capacity * (size_t)dex::chain_length(max_mip) * (size_t)(2 * W);
+    return n_batch * (size_t)capacity * (size_t)dex::chain_length(max_mip) * (size_t)dex::record_floats(W, storage);
 }
 
 int dex_grid_build(dex_ctx* ctx, int nx, int nz, int n_lambda, const float* eta, const float* chi,
@@ -343,6 +349,9 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
         return fail(ctx, DEX_ERR_ARG, "max_mip must be in [0, 4], got %d", params->max_mip);
     if (std::isnan(params->iod_eta) || std::isnan(params->iod_chi) || std::isnan(params->chi_ds_min))
         return fail(ctx, DEX_ERR_ARG, "NaN threshold");
+    if (!valid_storage(W, params->storage))
+        return fail(ctx, DEX_ERR_ARG, "storage %d not available for W = %d (bfloat16/float16 need W = 4 or 8)",
+                    params->storage, W);
     const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
     if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
     if (!eta || !chi || !active || !n_active || !bricks || !state_words) return fail(ctx, DEX_ERR_ARG, "null buffer");
@@ -359,6 +368,7 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
     P.chain = dex::chain_length(params->max_mip);
     P.n_words = (int)dex_state_words(nx, nz);
     P.cap_active = capacity;
+    P.storage = params->storage;
     P.log_mean = params->log_mean != 0;
     P.thr_eta = params->iod_eta;
     P.thr_chi = params->iod_chi;
@@ -377,7 +387,7 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
     return ok(ctx);
 }
 
-static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, int W, int max_mip,
+static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, int W, int max_mip, int storage,
                         const float* bricks, const unsigned long long* state_words, const int* block_offset,
                         const int* active, const int* n_active, int capacity, int n_dir, const float* dirs,
                         const float* weights, int n_band, const float* band, float i_bc, float* J, float* I,
@@ -388,10 +398,13 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
     if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
     if (max_mip < 0 || max_mip > 4) return fail(ctx, DEX_ERR_ARG, "max_mip must be in [0, 4]");
+    if (kind == 0 ? !valid_storage(W, storage) : storage != DEX_STORE_F32)
+        return fail(ctx, DEX_ERR_ARG, "storage %d not available here", storage);
     const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
     if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
     if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
     dex::HddaParams P{};
+    P.storage = storage;
     P.n_band = -1;
     if (band != nullptr && n_band >= 0) {
         if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);
@@ -436,13 +449,13 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_hdda launch");
     return ok(ctx);
 }
-int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
-                          const unsigned long long* state_words, const int* block_offset, const int* active,
-                          const int* n_active, int capacity, int n_dir, const float* dirs, const float* weights,
-                          int n_band, const float* band, float i_bc, float* J, float* I,
+int dex_formal_solve_hdda(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, int storage,
+                          const float* bricks, const unsigned long long* state_words, const int* block_offset,
+                          const int* active, const int* n_active, int capacity, int n_dir, const float* dirs,
+                          const float* weights, int n_band, const float* band, float i_bc, float* J, float* I,
                           unsigned long long* seg_count)
 {
-    return solve_sparse(ctx, 0, nx, nz, n_lambda, W, max_mip, bricks, state_words, block_offset, active, n_active,
+    return solve_sparse(ctx, 0, nx, nz, n_lambda, W, max_mip, storage, bricks, state_words, block_offset, active, n_active,
                         capacity, n_dir, dirs, weights, n_band, band, i_bc, J, I, seg_count);
 }
 
@@ -722,7 +735,7 @@ int dex_formal_solve_velinterp(dex_ctx* ctx, int nx, int nz, int n_lambda, int W
                                int n_band, const float* band, float i_bc, float* J, float* I,
                                unsigned long long* seg_count)
 {
-    return solve_sparse(ctx, 2, nx, nz, n_lambda, W, max_mip, bricks, state_words, block_offset, active, n_active,
+    return solve_sparse(ctx, 2, nx, nz, n_lambda, W, max_mip, DEX_STORE_F32, bricks, state_words, block_offset, active, n_active,
                         capacity, n_dir, dirs, weights, n_band, band, i_bc, J, I, seg_count);
 }
 

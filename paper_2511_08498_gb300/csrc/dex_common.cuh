@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "dexgb.h"
@@ -81,6 +83,40 @@ __device__ __forceinline__ void segment(float S, float chi, float nl2, float& I,
     T *= e;
 }
 
+// The same update for two wavelengths at once on the packed FP32 pipe
+// (FFMA2/FMUL2/FADD2 of sm_100+): every lane of a pair is rounded exactly as
+// in segment(), so results are bit-identical, with about half the FP32
+// instructions issued.
+__device__ __forceinline__ void segment2(float2 S, float2 chi, float nl2, float& I0, float& I1, float& T0,
+                                         float& T1)
+{
+    const float2 x = __fmul2_rn(chi, make_float2(nl2, nl2));
+    const float2 e = make_float2(ex2_approx(x.x), ex2_approx(x.y));
+    float2 p = __ffma2_rn(x, make_float2(kG5, kG5), make_float2(kG4, kG4));
+    p = __ffma2_rn(x, p, make_float2(kG3, kG3));
+    p = __ffma2_rn(x, p, make_float2(kG2, kG2));
+    p = __ffma2_rn(x, p, make_float2(kG1, kG1));
+    const float2 xp = __fmul2_rn(x, p);
+    const float2 ome = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-e.x, -e.y));
+    const float2 g = make_float2(x.x > kSeriesCut ? xp.x : ome.x, x.y > kSeriesCut ? xp.y : ome.y);
+    const float2 I = __ffma2_rn(make_float2(T0, T1), __fmul2_rn(S, g), make_float2(I0, I1));
+    const float2 T = __fmul2_rn(make_float2(T0, T1), e);
+    I0 = I.x;
+    I1 = I.y;
+    T0 = T.x;
+    T1 = T.y;
+}
+
+// All W wavelengths of a record: pairs on the packed pipe, an odd one alone.
+template <int W>
+__device__ __forceinline__ void segments(const float* S, const float* chi, float nl2, float* I, float* T)
+{
+#pragma unroll
+    for (int w = 0; w + 1 < W; w += 2)
+        segment2(make_float2(S[w], S[w + 1]), make_float2(chi[w], chi[w + 1]), nl2, I[w], I[w + 1], T[w], T[w + 1]);
+    if constexpr (W % 2 == 1) segment(S[W - 1], chi[W - 1], nl2, I[W - 1], T[W - 1]);
+}
+
 // Ray parameter of grid planes as an unevaluated sum hi + lo of two floats.
 // A plane at offset P (a half-integer, exact) from the origin along an axis
 // with direction component d is hit at t = P / d.  hi = P * ih is the rounded
@@ -145,6 +181,130 @@ __device__ __forceinline__ Record<W> load_record(const float* __restrict__ p)
     }
     return r;
 }
+
+// Storage formats of a static record (FP32 accumulation along the ray in all):
+//   F32  : S[W], chi[W] float32 (8W bytes)
+//   BF16 : S[W], chi[W] bfloat16, round to nearest even (4W bytes; W = 4, 8)
+//   F16  : float32 scales (max S, max chi of the record), 2 pad words, then
+//          S[W] / scaleS and chi[W] / scalechi as float16 (16 + 4W bytes; W = 4, 8)
+enum StorageFormat { kStoreF32 = 0, kStoreBF16 = 1, kStoreF16 = 2 };
+
+template <int W, int ST>
+struct RecFmt;
+
+template <int W>
+struct RecFmt<W, kStoreF32> {
+    static constexpr int kStride = 2 * W;  // floats
+    __device__ __forceinline__ static Record<W> load(const float* p) { return load_record<W>(p); }
+    __device__ __forceinline__ static void store(float* rec, const float* S, const float* chi)
+    {
+        if constexpr (W >= 2) {
+            float4* q = reinterpret_cast<float4*>(rec);
+            float v[2 * W];
+#pragma unroll
+            for (int w = 0; w < W; ++w) { v[w] = S[w]; v[W + w] = chi[w]; }
+#pragma unroll
+            for (int u = 0; u < (2 * W) / 4; ++u) q[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        } else {
+            *reinterpret_cast<float2*>(rec) = make_float2(S[0], chi[0]);
+        }
+    }
+};
+
+template <int W>
+struct RecFmt<W, kStoreBF16> {
+    static_assert(W == 4 || W == 8, "reduced-precision records need W = 4 or 8");
+    static constexpr int kStride = W;  // floats (2W bfloat16)
+    __device__ __forceinline__ static float lo(unsigned int u) { return __uint_as_float(u << 16); }
+    __device__ __forceinline__ static float hi(unsigned int u) { return __uint_as_float(u & 0xffff0000u); }
+    __device__ __forceinline__ static Record<W> load(const float* p)
+    {
+        Record<W> r;
+        const uint4* q = reinterpret_cast<const uint4*>(p);
+        unsigned int u[W];
+        if constexpr (W == 8) {
+            const uint4 a = __ldg(q), b = __ldg(q + 1);
+            u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w; u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+        } else {
+            const uint4 a = __ldg(q);
+            u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+        }
+#pragma unroll
+        for (int k = 0; k < W / 2; ++k) {
+            r.S[2 * k] = lo(u[k]);
+            r.S[2 * k + 1] = hi(u[k]);
+            r.chi[2 * k] = lo(u[W / 2 + k]);
+            r.chi[2 * k + 1] = hi(u[W / 2 + k]);
+        }
+        return r;
+    }
+    __device__ __forceinline__ static void store(float* rec, const float* S, const float* chi)
+    {
+        unsigned int u[W];
+#pragma unroll
+        for (int k = 0; k < W / 2; ++k) {
+            u[k] = (unsigned int)__bfloat16_as_ushort(__float2bfloat16_rn(S[2 * k])) |
+                   ((unsigned int)__bfloat16_as_ushort(__float2bfloat16_rn(S[2 * k + 1])) << 16);
+            u[W / 2 + k] = (unsigned int)__bfloat16_as_ushort(__float2bfloat16_rn(chi[2 * k])) |
+                           ((unsigned int)__bfloat16_as_ushort(__float2bfloat16_rn(chi[2 * k + 1])) << 16);
+        }
+        uint4* q = reinterpret_cast<uint4*>(rec);
+#pragma unroll
+        for (int k = 0; k < W / 4; ++k) q[k] = make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
+    }
+};
+
+template <int W>
+struct RecFmt<W, kStoreF16> {
+    static_assert(W == 4 || W == 8, "reduced-precision records need W = 4 or 8");
+    static constexpr int kStride = 4 + W;  // floats: 2 scales, 2 pad, 2W float16
+    __device__ __forceinline__ static float h(unsigned int u, int hi_half)
+    {
+        return __half2float(__ushort_as_half((unsigned short)(hi_half ? (u >> 16) : (u & 0xffffu))));
+    }
+    __device__ __forceinline__ static Record<W> load(const float* p)
+    {
+        Record<W> r;
+        const float4 hd = __ldg(reinterpret_cast<const float4*>(p));
+        const uint4* q = reinterpret_cast<const uint4*>(p + 4);
+        unsigned int u[W];
+        if constexpr (W == 8) {
+            const uint4 a = __ldg(q), b = __ldg(q + 1);
+            u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w; u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+        } else {
+            const uint4 a = __ldg(q);
+            u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+        }
+#pragma unroll
+        for (int k = 0; k < W / 2; ++k) {
+            r.S[2 * k] = h(u[k], 0) * hd.x;
+            r.S[2 * k + 1] = h(u[k], 1) * hd.x;
+            r.chi[2 * k] = h(u[W / 2 + k], 0) * hd.y;
+            r.chi[2 * k + 1] = h(u[W / 2 + k], 1) * hd.y;
+        }
+        return r;
+    }
+    __device__ __forceinline__ static void store(float* rec, const float* S, const float* chi)
+    {
+        float ms = 0.0f, mc = 0.0f;
+#pragma unroll
+        for (int w = 0; w < W; ++w) { ms = fmaxf(ms, S[w]); mc = fmaxf(mc, chi[w]); }
+        if (!(ms > 0.0f)) ms = 1.0f;
+        if (!(mc > 0.0f)) mc = 1.0f;
+        unsigned int u[W];
+#pragma unroll
+        for (int k = 0; k < W / 2; ++k) {
+            u[k] = (unsigned int)__half_as_ushort(__float2half_rn(S[2 * k] / ms)) |
+                   ((unsigned int)__half_as_ushort(__float2half_rn(S[2 * k + 1] / ms)) << 16);
+            u[W / 2 + k] = (unsigned int)__half_as_ushort(__float2half_rn(chi[2 * k] / mc)) |
+                           ((unsigned int)__half_as_ushort(__float2half_rn(chi[2 * k + 1] / mc)) << 16);
+        }
+        *reinterpret_cast<float4*>(rec) = make_float4(ms, mc, 0.0f, 0.0f);
+        uint4* q = reinterpret_cast<uint4*>(rec + 4);
+#pragma unroll
+        for (int k = 0; k < W / 4; ++k) q[k] = make_uint4(u[4 * k], u[4 * k + 1], u[4 * k + 2], u[4 * k + 3]);
+    }
+};
 
 // Quadrature passed by value to the solve kernels.
 struct Quadrature {

@@ -24,7 +24,7 @@ struct DenseParams {
 };
 
 struct MipParams {
-    int nx, nz, nbx, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active;
+    int nx, nz, nbx, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active, storage;
     bool log_mean;
     float thr_eta, thr_chi, chi_ds_min;
     const float* eta;
@@ -38,7 +38,7 @@ struct MipParams {
 };
 
 struct HddaParams {
-    int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active;
+    int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
     float band[4];
     long long n_cells;
@@ -147,6 +147,7 @@ cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, i
 cudaError_t noalloc_scratch(unsigned int** out);
 
 int chain_length(int max_mip);
+int record_floats(int W, int storage);
 cudaError_t launch_voigt(cudaStream_t s, long long n, const float* a, const float* x, float* h);
 cudaError_t launch_synth_static_line(cudaStream_t s, long long n_cells, int n_lambda, const float* chi_c,
                                      const float* s_c, const float* s_l, const float* ratio, const float* dld,

@@ -41,8 +41,7 @@ struct StaticRec {
     __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
                                                      float* I, float* T)
     {
-#pragma unroll
-        for (int w = 0; w < W; ++w) segment(v.S[w], v.chi[w], nl2, I[w], T[w]);
+        segments<W>(v.S, v.chi, nl2, I, T);
     }
 };
 

@@ -119,8 +119,7 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
             }
             const Record<W> r = load_record<W>(rp);
             const float nl2 = len * kNegLog2e;
-#pragma unroll
-            for (int w = 0; w < W; ++w) segment(r.S[w], r.chi[w], nl2, I[w], T[w]);
+            segments<W>(r.S, r.chi, nl2, I, T);
             if (COUNT) nseg += (th > th_prev);
             if (th >= t2) break;
             th_prev = th;

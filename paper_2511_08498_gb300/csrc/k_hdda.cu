@@ -27,21 +27,21 @@ namespace dex {
 
 namespace {
 
-// Static voxel model: a record holds (S, chi) for the W wavelengths of a batch.
-template <int W>
+// Static voxel model: a record holds (S, chi) for the W wavelengths of a batch,
+// stored in format ST (float32, bfloat16 or scaled float16; see RecFmt).
+template <int W, int ST = kStoreF32>
 struct StaticModel {
-    static constexpr int kStride = 2 * W;
+    static constexpr int kStride = RecFmt<W, ST>::kStride;
     static constexpr bool kPerBatch = true;
     struct Params {
         int unused;
     };
     using Voxel = Record<W>;
-    __device__ __forceinline__ static Voxel load(const float* p) { return load_record<W>(p); }
+    __device__ __forceinline__ static Voxel load(const float* p) { return RecFmt<W, ST>::load(p); }
     __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
                                                      float* I, float* T)
     {
-#pragma unroll
-        for (int w = 0; w < W; ++w) segment(v.S[w], v.chi[w], nl2, I[w], T[w]);
+        segments<W>(v.S, v.chi, nl2, I, T);
     }
 };
 
@@ -64,21 +64,41 @@ cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& P)
     const size_t smem = sizeof(unsigned long long) * (size_t)P.n_words;
     dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
     cudaError_t e = cudaSuccess;
-    switch (P.W) {
-#define DEX_LAUNCH(WW)                                                                   \
-    case WW:                                                                             \
-        if (P.seg_count) e = launch_hdda_kernel(k_solve_hdda_t<WW, true, StaticModel<WW>>, grid, smem, s, P, typename StaticModel<WW>::Params{}); \
-        else e = launch_hdda_kernel(k_solve_hdda_t<WW, false, StaticModel<WW>>, grid, smem, s, P, typename StaticModel<WW>::Params{}); \
+    switch (P.W * 4 + P.storage) {
+#define DEX_LAUNCH(WW, ST)                                                                                   \
+    case WW * 4 + ST:                                                                                        \
+        if (P.seg_count)                                                                                     \
+            e = launch_hdda_kernel(k_solve_hdda_t<WW, true, StaticModel<WW, ST>>, grid, smem, s, P,          \
+                                   typename StaticModel<WW, ST>::Params{});                                  \
+        else                                                                                                 \
+            e = launch_hdda_kernel(k_solve_hdda_t<WW, false, StaticModel<WW, ST>>, grid, smem, s, P,         \
+                                   typename StaticModel<WW, ST>::Params{});                                  \
         break;
-        DEX_LAUNCH(1)
-        DEX_LAUNCH(2)
-        DEX_LAUNCH(4)
-        DEX_LAUNCH(8)
+        DEX_LAUNCH(1, kStoreF32)
+        DEX_LAUNCH(2, kStoreF32)
+        DEX_LAUNCH(4, kStoreF32)
+        DEX_LAUNCH(8, kStoreF32)
+        DEX_LAUNCH(4, kStoreBF16)
+        DEX_LAUNCH(8, kStoreBF16)
+        DEX_LAUNCH(4, kStoreF16)
+        DEX_LAUNCH(8, kStoreF16)
 #undef DEX_LAUNCH
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+}  // namespace dex
+
+namespace dex {
+
+int record_floats(int W, int storage)
+{
+    if (storage == kStoreF32) return 2 * W;
+    if (storage == kStoreBF16) return W;
+    if (storage == kStoreF16) return 4 + W;
+    return 0;
 }
 
 }  // namespace dex

@@ -14,8 +14,9 @@
 // The block level is the largest m <= max_mip such that every group at every
 // level <= m passes for every wavelength of the batch, optionally capped per
 // block.  Every level of the chain is written as wavelength-batch records
-// (S, chi); the level goes into the packed 3-bit state words (0 = empty,
-// m + 1 = level m, 21 blocks per 64-bit word).
+// (S, chi) in the requested storage format (float32, bfloat16, or float16 with
+// per-record scales); the level goes into the packed 3-bit state words
+// (0 = empty, m + 1 = level m, 21 blocks per 64-bit word).
 #include "vlm.cuh"
 
 namespace dex {
@@ -26,24 +27,19 @@ constexpr int kMaxLevels = 5;  // levels 0..4 of a 16 x 16 block
 
 __host__ __device__ constexpr int level_offset(int m) { return 341 - (341 >> (2 * m)); }
 
-template <int W>
+template <int W, int ST>
 __device__ __forceinline__ void store_record(float* rec, const float* e, const float* c)
 {
-    float v[2 * W];
+    float S[W], x[W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) encode_voxel(e[w], c[w], v[w], v[W + w]);
-    if constexpr (W >= 2) {
-        float4* q = reinterpret_cast<float4*>(rec);
-#pragma unroll
-        for (int u = 0; u < (2 * W) / 4; ++u) q[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-    } else {
-        *reinterpret_cast<float2*>(rec) = make_float2(v[0], v[1]);
-    }
+    for (int w = 0; w < W; ++w) encode_voxel(e[w], c[w], S[w], x[w]);
+    RecFmt<W, ST>::store(rec, S, x);
 }
 
-template <int W>
+template <int W, int ST>
 __global__ void __launch_bounds__(256) k_mips_build(const MipParams P)
 {
+    constexpr int REC = RecFmt<W, ST>::kStride;
     // level m values: sm_e[level][w][voxel], voxel count (16 >> m)^2
     __shared__ float sm_e[level_offset(kMaxLevels)][W];
     __shared__ float sm_c[level_offset(kMaxLevels)][W];
@@ -56,7 +52,7 @@ __global__ void __launch_bounds__(256) k_mips_build(const MipParams P)
     const int x = bx * DEX_BLOCK + (t & 15), z = bz * DEX_BLOCK + (t >> 4);
     const long long c = (long long)z * P.nx + x;
     const long long n_cells = (long long)P.nx * P.nz;
-    float* brick = P.bricks + ((size_t)b * P.cap_active + a) * P.chain * (2 * W);
+    float* brick = P.bricks + ((size_t)b * P.cap_active + a) * P.chain * REC;
 
     // level 0
     {
@@ -81,7 +77,7 @@ __global__ void __launch_bounds__(256) k_mips_build(const MipParams P)
             sm_c[t][w] = cv;
         }
         if (bad) raise_status(P.status, DEX_ERR_NUMERIC);
-        store_record<W>(brick + (size_t)t * (2 * W), e, x_);
+        store_record<W, ST>(brick + (size_t)t * REC, e, x_);
     }
     __syncthreads();
 
@@ -112,7 +108,7 @@ __global__ void __launch_bounds__(256) k_mips_build(const MipParams P)
                 sm_e[off + t][w] = se.val;
                 sm_c[off + t][w] = sc.val;
             }
-            store_record<W>(brick + (size_t)(off + t) * (2 * W), e, x_);
+            store_record<W, ST>(brick + (size_t)(off + t) * REC, e, x_);
         }
         const int all = __syncthreads_and(pass ? 1 : 0);
         if (ok && all) level = m;
@@ -139,11 +135,16 @@ cudaError_t launch_mips_build(cudaStream_t s, const MipParams& P)
     cudaError_t e = cudaMemsetAsync(P.words, 0, sizeof(unsigned long long) * (size_t)P.n_words * P.n_batch, s);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
-    switch (P.W) {
-        case 1: k_mips_build<1><<<grid, 256, 0, s>>>(P); break;
-        case 2: k_mips_build<2><<<grid, 256, 0, s>>>(P); break;
-        case 4: k_mips_build<4><<<grid, 256, 0, s>>>(P); break;
-        case 8: k_mips_build<8><<<grid, 256, 0, s>>>(P); break;
+    const int key = P.W * 4 + P.storage;
+    switch (key) {
+        case 1 * 4 + kStoreF32: k_mips_build<1, kStoreF32><<<grid, 256, 0, s>>>(P); break;
+        case 2 * 4 + kStoreF32: k_mips_build<2, kStoreF32><<<grid, 256, 0, s>>>(P); break;
+        case 4 * 4 + kStoreF32: k_mips_build<4, kStoreF32><<<grid, 256, 0, s>>>(P); break;
+        case 8 * 4 + kStoreF32: k_mips_build<8, kStoreF32><<<grid, 256, 0, s>>>(P); break;
+        case 4 * 4 + kStoreBF16: k_mips_build<4, kStoreBF16><<<grid, 256, 0, s>>>(P); break;
+        case 8 * 4 + kStoreBF16: k_mips_build<8, kStoreBF16><<<grid, 256, 0, s>>>(P); break;
+        case 4 * 4 + kStoreF16: k_mips_build<4, kStoreF16><<<grid, 256, 0, s>>>(P); break;
+        case 8 * 4 + kStoreF16: k_mips_build<8, kStoreF16><<<grid, 256, 0, s>>>(P); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
