@@ -7,7 +7,7 @@ line-profile evaluation, no ray traversal, no mipmapping.  Both the oracle and
 the CUDA path start from the float32 arrays returned here.
 """
 
-from . import atom  # noqa: F401
+from . import atom, mlp  # noqa: F401
 from .atmospheres import (  # noqa: F401
     SEED_BASE,
     lognormal_field,
