@@ -39,7 +39,8 @@ enum {
     DEX_ERR_CUDA = 2,           /* a CUDA runtime call failed                         */
     DEX_ERR_TRAVERSAL_CAP = 4,  /* device: a ray exceeded its traversal step cap      */
     DEX_ERR_NUMERIC = 8,        /* device: negative or non-finite opacity/emissivity  */
-    DEX_ERR_UNSUPPORTED = 16    /* configuration outside the compiled variants        */
+    DEX_ERR_UNSUPPORTED = 16,   /* configuration outside the compiled variants        */
+    DEX_ERR_TIMEOUT = 32        /* device: a bounded wait on the tensor cores expired  */
 };
 
 #define DEX_VERSION 100
@@ -368,6 +369,20 @@ int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int 
                          const float* dirs, const float* weights, int n_band, const float* band, float i_bc,
                          float* J, float* I, unsigned long long* seg_count);
 
+/* The Core-and-Voigt solve with the learned surrogate network (see
+ * dex_mlp_forward below) as the line profile: inside the network's training
+ * domain (1e-3 <= a' <= 1e-1, |x| <= 16, |u| <= 10 with x = dv / v_th,
+ * a' = a / s^2, u = -(v . w) / v_th) H = exp(network(x, a', u)), evaluated in
+ * float32 on the CUDA cores with W1, W2, w3 rounded to bfloat16; outside it the
+ * HUM1WEI24 evaluation of dex_formal_solve_cav.  mlp_params: HOST array of
+ * dex_mlp_param_count() floats (copied into the launch; non-finite -> DEX_ERR_ARG).
+ * Other arguments as dex_formal_solve_cav.  The paper has no counterpart. */
+int dex_formal_solve_cav_mlp(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv,
+                             float c_kms, const float* bricks, const unsigned long long* state_words,
+                             const int* block_offset, const int* active, const int* n_active, int capacity,
+                             int n_dir, const float* dirs, const float* weights, int n_band, const float* band,
+                             float i_bc, const float* mlp_params, float* J, float* I, unsigned long long* seg_count);
+
 /* --------------------------------------------------- velocity interpolation --
  *
  * Section 3.1 with the line model above: every MIP voxel (MIP 0 included)
@@ -467,6 +482,49 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
 
 int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, int ctas,
                             unsigned long long* done_ns, unsigned long long* start_ns);
+
+/* ------------------------------------------------------------------------
+ * Learned Voigt-profile surrogate.  The paper evaluates the Voigt profile of
+ * the Core-and-Voigt treatment on the fly (Section 3.2); this library adds a
+ * small network trained on the profiles that evaluation produces, as an
+ * alternative to it.  The paper has no counterpart of these calls.
+ *
+ * Network: features f = (x / 16, log10(a) + 2, u / 16) of the wavelength offset
+ * x from line centre in Doppler widths (rest frame), the damping a and the
+ * projected velocity u in Doppler widths; h1 = GELU(W1 f + b1) (64),
+ * h2 = GELU(W2 h1 + b2) (64), y = w3 . h2 + b3 predicts ln H(a, x - u).
+ * GELU(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+ * Parameters: one float32 array of dex_mlp_param_count() = 4481 values:
+ *   W1 [64][3] at 0, b1 [64] at 192, W2 [64][64] (row = output) at 256,
+ *   b2 [64] at 4352, w3 [64] at 4416, b3 at 4480.
+ * The kernels use W1, W2, w3 rounded to bfloat16 (round to nearest even) and
+ * the bfloat16-rounded h1 as tensor-core operands; all sums are float32.
+ * Samples xau are [n][3] float32 (x, a, u), device memory.  A sample with a
+ * non-finite value or a <= 0 is skipped and sets DEX_ERR_NUMERIC.
+ * ---------------------------------------------------------------------- */
+int dex_mlp_param_count(void);
+
+/* ln H predictions out[n] (device) for n >= 0 samples. */
+int dex_mlp_forward(dex_ctx* ctx, long long n, const float* xau, const float* params, float* out);
+
+/* Mean squared error L = (1/n) sum (y - target)^2 over n >= 0 samples and its
+ * gradient with respect to every parameter: grad (device, dex_mlp_param_count()
+ * floats) and loss (device, one float) are overwritten.  Gradients through the
+ * tensor cores use bfloat16 operands: the per-sample output errors of layer 2
+ * (delta2 = dy w3 GELU'(z2)), dy h2, the layer-1 errors and the features. */
+int dex_mlp_grad(dex_ctx* ctx, long long n, const float* xau, const float* target, const float* params,
+                 float* grad, float* loss);
+
+/* One Adam step (Kingma & Ba 2015) on the float32 parameters, step >= 1:
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * p -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * All arrays device memory of dex_mlp_param_count() floats. */
+int dex_mlp_adam(dex_ctx* ctx, float* params, const float* grad, float* m, float* v, int step, float lr,
+                 float beta1, float beta2, float eps);
+
+/* Training targets ln H(a, x - u) from the library's own Voigt evaluation
+ * (dex_voigt's scheme), out[n] device. */
+int dex_mlp_targets(dex_ctx* ctx, long long n, const float* xau, float* out);
 
 #ifdef __cplusplus
 }

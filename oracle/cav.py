@@ -41,11 +41,12 @@ def param_arrays(m):
     return np.stack([vals[k] for k in PARAMS])
 
 
-def eta_chi(P, dv, wx, wz, c_kms, method="exact", closest_to_core=False):
+def eta_chi(P, dv, wx, wz, c_kms, method="exact", closest_to_core=False, profile=None):
     """eta, chi [L][...] from parameters P [8][...] for propagation direction (wx, wz).
 
     With ``closest_to_core`` the projected velocity is replaced by the shift within
-    [-|v|, |v|] closest to line centre (direction-free worst case of Section 3.2)."""
+    [-|v|, |v|] closest to line centre (direction-free worst case of Section 3.2).
+    ``profile(a, x, u)``, if given, replaces H(a, x - u) (x = dv / v_th, u = -(v.w) / v_th)."""
     es, cs, a, inv, vx, vz, ec, cc = P
     dv = np.asarray(dv, dtype=np.float64)
     L = dv.size
@@ -58,7 +59,10 @@ def eta_chi(P, dv, wx, wz, c_kms, method="exact", closest_to_core=False):
             u = np.maximum(np.abs(dv[k]) - speed, 0.0)
         else:
             u = dv[k] + vx * wx + vz * wz
-        H = voigt_h(a / (s * s), u * inv, method=method)
+        if profile is not None and not closest_to_core:
+            H = profile(a / (s * s), dv[k] * inv, -(vx * wx + vz * wz) * inv)
+        else:
+            H = voigt_h(a / (s * s), u * inv, method=method)
         phi = H * inv / np.sqrt(np.pi)
         eta[k] = es * s * phi + ec
         chi[k] = cs * s * phi + cc
@@ -94,7 +98,7 @@ def block_levels(chain, dv, c_kms, empty, block, lambda_batch, thr_eta, thr_chi,
 
 
 def formal_solve(P_levels, level_map, block, lambda_batch, dv, c_kms, dirs, weights, probes, band=None,
-                 method="hum1wei24_cf", i_bc=0.0, want_intensity=False):
+                 method="hum1wei24_cf", i_bc=0.0, want_intensity=False, profile=None):
     """Accelerated CaV result (or the plain one with a single level and all-zero map).
 
     P_levels: parameter chain (list of [8][nz>>m][nx>>m]); level_map [n_batch][nbz][nbx].
@@ -109,7 +113,7 @@ def formal_solve(P_levels, level_map, block, lambda_batch, dv, c_kms, dirs, weig
     I = np.zeros((L, dirs.shape[0], n_probe)) if want_intensity else None
     for k in range(dirs.shape[0]):
         wx, wz = -dirs[k, 0], -dirs[k, 1]
-        levels = [eta_chi(P, dv, wx, wz, c_kms, method=method) for P in P_levels]
+        levels = [eta_chi(P, dv, wx, wz, c_kms, method=method, profile=profile) for P in P_levels]
         if band is None:
             e2, c2 = omips.expand(levels, level_map, lambda_batch)
             _, Ik = lc.formal_solve(e2, c2, dirs[k:k + 1], [1.0], probes=probes, i_bc=i_bc, want_intensity=True)

@@ -111,3 +111,39 @@ def adam_step(p, g, m, v, step: int, lr: float, b1: float = 0.9, b2: float = 0.9
     mh = m / (1.0 - b1 ** step)
     vh = v / (1.0 - b2 ** step)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# training domain of the surrogate; outside it the exact evaluation is used
+X_MAX, U_MAX, A_MIN, A_MAX = 16.0, 10.0, 1e-3, 1e-1
+
+
+def weights_bf16(p):
+    """Parameters with W1, W2, w3 rounded to bfloat16 (biases untouched)."""
+    q = np.asarray(p, dtype=np.float64).copy()
+    for a, b in ((0, 192), (256, 4352), (4416, 4480)):
+        q[a:b] = bf16(q[a:b])
+    return q
+
+
+def profile_with_fallback(p, method="hum1wei24_cf"):
+    """H(a, x, u) of the Core-and-Voigt solve with the surrogate: exp(network) inside
+    the training domain (decided on float32 values, as the kernel does), the Voigt
+    function of ``method`` at x - u outside it.  The network runs in float64 with
+    bfloat16-rounded weights and unrounded activations (the in-solve evaluation)."""
+    from .voigt import voigt_h
+    q = weights_bf16(p)
+
+    def H(a, x, u):
+        a, x, u = (np.asarray(v, dtype=np.float64) for v in (a, x, u))
+        shape = np.broadcast(a, x, u).shape
+        a, x, u = (np.broadcast_to(v, shape).reshape(-1) for v in (a, x, u))
+        a32, x32, u32 = a.astype(np.float32), x.astype(np.float32), u.astype(np.float32)
+        inside = (a32 >= np.float32(A_MIN)) & (a32 <= np.float32(A_MAX)) & (np.abs(x32) <= X_MAX) & (np.abs(u32) <= U_MAX)
+        out = np.empty(a.size)
+        if inside.any():
+            xau = np.stack([x[inside], a[inside], u[inside]], axis=1)
+            out[inside] = np.exp(forward(q, xau, emulate=False))
+        if (~inside).any():
+            out[~inside] = voigt_h(a[~inside], x[~inside] - u[~inside], method=method)
+        return out.reshape(shape)
+    return H

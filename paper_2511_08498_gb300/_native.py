@@ -55,6 +55,9 @@ PROTOTYPES = {
     "dex_formal_solve_cav": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_fp, c_float, c_void_p, c_void_p,
                                      c_void_p, c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float,
                                      c_void_p, c_void_p, c_void_p]),
+    "dex_formal_solve_cav_mlp": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_fp, c_float, c_void_p,
+                                         c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int,
+                                         c_fp, c_float, c_fp, c_void_p, c_void_p, c_void_p]),
     "dex_vel_brick_floats": (c_size_t, [c_int, c_int, c_int, c_int]),
     "dex_vel_mips_build": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int, c_int, c_fp, c_float, c_void_p, c_void_p,
                                    c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -63,6 +66,12 @@ PROTOTYPES = {
                                            c_void_p, c_void_p, c_void_p]),
     "dex_batch_solve": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
     "dex_batch_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "dex_mlp_param_count": (c_int, []),
+    "dex_mlp_forward": (c_int, [c_void_p, ctypes.c_longlong, c_void_p, c_void_p, c_void_p]),
+    "dex_mlp_grad": (c_int, [c_void_p, ctypes.c_longlong, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "dex_mlp_adam": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float,
+                             ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "dex_mlp_targets": (c_int, [c_void_p, ctypes.c_longlong, c_void_p, c_void_p]),
 }
 
 

@@ -441,8 +441,13 @@ def cav_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: floa
 
 
 def formal_solve_cav(ctx: Context, grid: SparseGrid, mips: CavMips, dirs, weights, band=None, i_bc: float = 0.0,
-                     want_intensity: bool = False, count_segments: bool = False, J: torch.Tensor | None = None):
-    """Core-and-Voigt solve (``dex_formal_solve_cav``); outputs as :func:`formal_solve_hdda`."""
+                     want_intensity: bool = False, count_segments: bool = False, J: torch.Tensor | None = None,
+                     mlp_params=None):
+    """Core-and-Voigt solve (``dex_formal_solve_cav``); outputs as :func:`formal_solve_hdda`.
+
+    ``mlp_params`` (the surrogate network's parameters, any array-like; copied to
+    the host) selects ``dex_formal_solve_cav_mlp``: the network as the profile
+    inside its training domain, the exact evaluation outside it."""
     d, w = _quadrature(dirs, weights)
     dev = mips.bricks.device
     n_cells = grid.nx * grid.nz
@@ -453,11 +458,19 @@ def formal_solve_cav(ctx: Context, grid: SparseGrid, mips: CavMips, dirs, weight
     seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
     fp = ctypes.POINTER(ctypes.c_float)
     b = None if band is None else _host_f32(band).reshape(-1)
-    ctx._rc(lib().dex_formal_solve_cav(
-        ctx.handle, grid.nx, grid.nz, L, mips.W, mips.max_mip, mips.dv.ctypes.data_as(fp), mips.c_kms,
-        _ptr(mips.bricks), _ptr(mips.words), _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev),
-        mips.capacity, d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
-        None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+    common = (ctx.handle, grid.nx, grid.nz, L, mips.W, mips.max_mip, mips.dv.ctypes.data_as(fp), mips.c_kms,
+              _ptr(mips.bricks), _ptr(mips.words), _ptr(grid.block_offset), _ptr(grid.active),
+              _ptr(grid.n_active_dev), mips.capacity, d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp),
+              -1 if b is None else b.size, None if b is None else b.ctypes.data_as(fp), float(i_bc))
+    if mlp_params is None:
+        ctx._rc(lib().dex_formal_solve_cav(*common, _ptr(J), _ptr(I), _ptr(seg)))
+    else:
+        if isinstance(mlp_params, torch.Tensor):
+            mlp_params = mlp_params.detach().cpu().numpy()
+        net = _host_f32(mlp_params).reshape(-1)
+        if net.size != mlp_param_count():
+            raise ValueError(f"expected {mlp_param_count()} network parameters, got {net.size}")
+        ctx._rc(lib().dex_formal_solve_cav_mlp(*common, net.ctypes.data_as(fp), _ptr(J), _ptr(I), _ptr(seg)))
     return J, I, seg
 
 
@@ -569,3 +582,78 @@ def batch_solve_noalloc(ctx: Context, items, W: int, ctas: int = 0, done_ns: tor
     ``start_ns`` [1] int64 tensors to get completion times."""
     arr = (BatchItem * len(items))(*items)
     ctx._rc(lib().dex_batch_solve_noalloc(ctx.handle, len(items), arr, W, int(ctas), _ptr(done_ns), _ptr(start_ns)))
+
+
+# ------------------------------------------------------ profile surrogate --
+
+def mlp_param_count() -> int:
+    return int(lib().dex_mlp_param_count())
+
+
+def _samples(xau):
+    if xau.dim() != 2 or xau.shape[1] != 3 or xau.dtype != torch.float32 or not xau.is_contiguous():
+        raise ValueError("xau must be a contiguous [n][3] float32 tensor")
+    return xau.shape[0]
+
+
+def mlp_forward(ctx: Context, xau: torch.Tensor, params: torch.Tensor, out: torch.Tensor | None = None):
+    """Predicted ln H(a, x - u) of the surrogate network (``dex_mlp_forward``)."""
+    n = _samples(xau)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=xau.device)
+    ctx._rc(lib().dex_mlp_forward(ctx.handle, n, _ptr(xau), _ptr(params), _ptr(out)))
+    return out
+
+
+def mlp_grad(ctx: Context, xau: torch.Tensor, target: torch.Tensor, params: torch.Tensor,
+             grad: torch.Tensor | None = None, loss: torch.Tensor | None = None):
+    """Mean squared error and its gradient (``dex_mlp_grad``); returns ``(grad, loss)``."""
+    n = _samples(xau)
+    if grad is None:
+        grad = torch.empty(mlp_param_count(), dtype=torch.float32, device=xau.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=xau.device)
+    ctx._rc(lib().dex_mlp_grad(ctx.handle, n, _ptr(xau), _ptr(target), _ptr(params), _ptr(grad), _ptr(loss)))
+    return grad, loss
+
+
+def mlp_adam(ctx: Context, params, grad, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+             eps: float = 1e-8):
+    """One Adam step in place on ``params`` (``dex_mlp_adam``)."""
+    ctx._rc(lib().dex_mlp_adam(ctx.handle, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr),
+                               float(beta1), float(beta2), float(eps)))
+
+
+def mlp_targets(ctx: Context, xau: torch.Tensor, out: torch.Tensor | None = None):
+    """ln H(a, x - u) from the library's Voigt evaluation (``dex_mlp_targets``)."""
+    n = _samples(xau)
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=xau.device)
+    ctx._rc(lib().dex_mlp_targets(ctx.handle, n, _ptr(xau), _ptr(out)))
+    return out
+
+
+def mlp_train(ctx: Context, xau: torch.Tensor, target: torch.Tensor, params: torch.Tensor, steps: int,
+              batch: int, lr: float = 1e-3, lr_final: float | None = None, log_every: int = 0):
+    """Minibatch Adam on the surrogate: each step is ``dex_mlp_grad`` on the next
+    contiguous slice of the (caller-shuffled) samples, then ``dex_mlp_adam``.  The
+    learning rate decays geometrically from ``lr`` to ``lr_final`` (default: constant).
+    Returns the per-step losses logged every ``log_every`` steps (float list)."""
+    n = _samples(xau)
+    P = mlp_param_count()
+    m = torch.zeros(P, dtype=torch.float32, device=xau.device)
+    v = torch.zeros_like(m)
+    grad = torch.empty_like(m)
+    loss = torch.empty(1, dtype=torch.float32, device=xau.device)
+    logged = []
+    ratio = 1.0 if lr_final is None else (lr_final / lr) ** (1.0 / max(1, steps - 1))
+    off = 0
+    for k in range(steps):
+        if off + batch > n:
+            off = 0
+        mlp_grad(ctx, xau[off:off + batch], target[off:off + batch], params, grad=grad, loss=loss)
+        mlp_adam(ctx, params, grad, m, v, k + 1, lr * ratio ** k)
+        off += batch
+        if log_every and (k % log_every == 0 or k == steps - 1):
+            logged.append(float(loss.item()))
+    return logged

@@ -128,6 +128,17 @@ int fill_atom(dex_ctx* ctx, const dex_atom* atom, int n_lambda, const double* la
     return DEX_OK;
 }
 
+// float -> nearest bfloat16 (ties to even), as a float; finite inputs
+float bf16_round_host(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+}
+
 }  // namespace
 
 extern "C" {
@@ -143,6 +154,7 @@ const char* dex_status_string(int s)
         case DEX_ERR_TRAVERSAL_CAP: return "ray traversal exceeded its step cap";
         case DEX_ERR_NUMERIC: return "negative or non-finite emissivity/opacity";
         case DEX_ERR_UNSUPPORTED: return "unsupported configuration";
+        case DEX_ERR_TIMEOUT: return "a bounded device-side wait expired";
         default: return "combined device error bits";
     }
 }
@@ -198,8 +210,8 @@ int dex_ctx_check(dex_ctx* ctx)
     e = cudaMemcpy(&h, ctx->status, sizeof(h), cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemset(ctx->status, 0, sizeof(h));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "status readback");
-    if (h) return fail(ctx, (int)h, "device reported: %s%s", (h & DEX_ERR_TRAVERSAL_CAP) ? "traversal cap " : "",
-                       (h & DEX_ERR_NUMERIC) ? "numeric" : "");
+    if (h) return fail(ctx, (int)h, "device reported: %s%s%s", (h & DEX_ERR_TRAVERSAL_CAP) ? "traversal cap " : "",
+                       (h & DEX_ERR_NUMERIC) ? "numeric " : "", (h & DEX_ERR_TIMEOUT) ? "wait timeout" : "");
     return ok(ctx);
 }
 
@@ -663,11 +675,11 @@ int dex_vel_mips_build(dex_ctx* ctx, int nx, int nz, const dex_cav_fields* field
                              level_cap, bricks, state_words);
 }
 
-int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv,
-                         float c_kms, const float* bricks, const unsigned long long* state_words,
-                         const int* block_offset, const int* active, const int* n_active, int capacity, int n_dir,
-                         const float* dirs, const float* weights, int n_band, const float* band, float i_bc,
-                         float* J, float* I, unsigned long long* seg_count)
+static int solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv, float c_kms,
+                     const float* bricks, const unsigned long long* state_words, const int* block_offset,
+                     const int* active, const int* n_active, int capacity, int n_dir, const float* dirs,
+                     const float* weights, int n_band, const float* band, float i_bc, float* J, float* I,
+                     unsigned long long* seg_count, const float* mlp_params)
 {
     if (!ctx) return DEX_ERR_ARG;
     if (int r = check_sparse_grid(ctx, nx, nz)) return r;
@@ -713,20 +725,54 @@ int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int 
     P.I = I;
     P.seg_count = seg_count;
     P.status = ctx->status;
-    dex::CavParams* M = new (std::nothrow) dex::CavParams();
+    dex::CavMlpParams* M = new (std::nothrow) dex::CavMlpParams();
     if (!M) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
-    dex::fill_cav_params(*M, n_lambda, W, dv, c_kms);
+    dex::fill_cav_params(M->cav, n_lambda, W, dv, c_kms);
+    if (mlp_params) {
+        const int n = dex::mlp_param_count();
+        for (int q = 0; q < n; ++q) {
+            if (!std::isfinite(mlp_params[q])) {
+                delete M;
+                return fail(ctx, DEX_ERR_ARG, "network parameter %d not finite", q);
+            }
+            const bool weight = q < 192 || (q >= 256 && q < 4352) || (q >= 4416 && q < 4480);
+            M->w[q] = weight ? bf16_round_host(mlp_params[q]) : mlp_params[q];
+        }
+    }
     int r = bind(ctx);
     if (!r) {
         cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
         if (e == cudaSuccess && I)
             e = cudaMemsetAsync(I, 0, sizeof(float) * (size_t)n_lambda * (size_t)n_dir * (size_t)P.n_cells,
                                 ctx->stream);
-        if (e == cudaSuccess) e = dex::launch_solve_cav(ctx->stream, P, *M);
+        if (e == cudaSuccess)
+            e = mlp_params ? dex::launch_solve_cav_mlp(ctx->stream, P, *M) : dex::launch_solve_cav(ctx->stream, P, M->cav);
         r = e != cudaSuccess ? cuda_fail(ctx, e, "solve_cav launch") : ok(ctx);
     }
     delete M;
     return r;
+}
+
+int dex_formal_solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv,
+                         float c_kms, const float* bricks, const unsigned long long* state_words,
+                         const int* block_offset, const int* active, const int* n_active, int capacity, int n_dir,
+                         const float* dirs, const float* weights, int n_band, const float* band, float i_bc,
+                         float* J, float* I, unsigned long long* seg_count)
+{
+    return solve_cav(ctx, nx, nz, n_lambda, W, max_mip, dv, c_kms, bricks, state_words, block_offset, active,
+                     n_active, capacity, n_dir, dirs, weights, n_band, band, i_bc, J, I, seg_count, nullptr);
+}
+
+int dex_formal_solve_cav_mlp(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* dv,
+                             float c_kms, const float* bricks, const unsigned long long* state_words,
+                             const int* block_offset, const int* active, const int* n_active, int capacity,
+                             int n_dir, const float* dirs, const float* weights, int n_band, const float* band,
+                             float i_bc, const float* mlp_params, float* J, float* I, unsigned long long* seg_count)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (!mlp_params) return fail(ctx, DEX_ERR_ARG, "null network parameters");
+    return solve_cav(ctx, nx, nz, n_lambda, W, max_mip, dv, c_kms, bricks, state_words, block_offset, active,
+                     n_active, capacity, n_dir, dirs, weights, n_band, band, i_bc, J, I, seg_count, mlp_params);
 }
 
 int dex_formal_solve_velinterp(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, const float* bricks,
@@ -851,3 +897,70 @@ int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms,
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ MLP --
+int dex_mlp_param_count(void) { return dex::mlp_param_count(); }
+
+int dex_mlp_forward(dex_ctx* ctx, long long n, const float* xau, const float* params, float* out)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (n < 0) return fail(ctx, DEX_ERR_ARG, "negative n");
+    if (n == 0) return ok(ctx);
+    if (!xau || !params || !out) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    dex::MlpParams P{};
+    P.n = n;
+    P.xau = xau;
+    P.params = params;
+    P.out = out;
+    P.status = ctx->status;
+    cudaError_t e = dex::launch_mlp_forward(ctx->stream, P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp forward launch");
+    return ok(ctx);
+}
+
+int dex_mlp_grad(dex_ctx* ctx, long long n, const float* xau, const float* target, const float* params,
+                 float* grad, float* loss)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (n < 0) return fail(ctx, DEX_ERR_ARG, "negative n");
+    if (!params || !grad || !loss || (n > 0 && (!xau || !target))) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    dex::MlpParams P{};
+    P.n = n;
+    P.xau = xau;
+    P.target = target;
+    P.params = params;
+    P.grad = grad;
+    P.loss = loss;
+    P.status = ctx->status;
+    cudaError_t e = dex::launch_mlp_grad(ctx->stream, P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp gradient launch");
+    return ok(ctx);
+}
+
+int dex_mlp_adam(dex_ctx* ctx, float* params, const float* grad, float* m, float* v, int step, float lr,
+                 float beta1, float beta2, float eps)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (!params || !grad || !m || !v) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (step < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+        !(eps > 0.0f))
+        return fail(ctx, DEX_ERR_ARG, "invalid Adam hyper-parameters");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_mlp_adam(ctx->stream, params, grad, m, v, step, lr, beta1, beta2, eps);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp adam launch");
+    return ok(ctx);
+}
+
+int dex_mlp_targets(dex_ctx* ctx, long long n, const float* xau, float* out)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (n < 0) return fail(ctx, DEX_ERR_ARG, "negative n");
+    if (n == 0) return ok(ctx);
+    if (!xau || !out) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_mlp_targets(ctx->stream, n, xau, out);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp targets launch");
+    return ok(ctx);
+}

@@ -95,6 +95,13 @@ struct CavParams {
     float is2[DEX_MAX_CAV_LAMBDA];  // (lambda / lambda0)^2
 };
 
+// Core-and-Voigt with the learned profile: the CaV tables plus the network's
+// parameters (W1, W2, w3 rounded to bfloat16 values), passed by value
+struct CavMlpParams {
+    CavParams cav;
+    float w[4481];
+};
+
 struct CavMipParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active;
     float thr_eta, thr_chi, chi_ds_min;
@@ -113,6 +120,7 @@ cudaError_t launch_cav_grid_build(cudaStream_t s, int nx, int nz, const CavField
                                   int* n_active);
 cudaError_t launch_cav_mips_build(cudaStream_t s, const CavMipParams& P, const CavParams& M);
 cudaError_t launch_solve_cav(cudaStream_t s, const HddaParams& P, const CavParams& M);
+cudaError_t launch_solve_cav_mlp(cudaStream_t s, const HddaParams& P, const CavMlpParams& M);
 
 int vel_record_floats(int W);
 cudaError_t launch_vel_mips_build(cudaStream_t s, const CavMipParams& P, const CavParams& M);
@@ -148,6 +156,24 @@ cudaError_t noalloc_scratch(unsigned int** out);
 
 int chain_length(int max_mip);
 int record_floats(int W, int storage);
+// learned profile surrogate (k_mlp.cu)
+struct MlpParams {
+    long long n;                 // samples
+    const float* xau;            // [n][3]: x, a, u
+    const float* target;         // [n] ln H (training)
+    const float* params;         // mlp_param_count() FP32 master parameters
+    float* out;                  // [n] predicted ln H (inference)
+    float* grad;                 // mlp_param_count() gradient of the mean loss (training)
+    float* loss;                 // mean squared error (training)
+    unsigned int* status;
+};
+int mlp_param_count();
+cudaError_t launch_mlp_forward(cudaStream_t s, const MlpParams& P);
+cudaError_t launch_mlp_grad(cudaStream_t s, const MlpParams& P);
+cudaError_t launch_mlp_adam(cudaStream_t s, float* p, const float* g, float* m, float* v, int step, float lr,
+                            float b1, float b2, float eps);
+cudaError_t launch_mlp_targets(cudaStream_t s, long long n, const float* xau, float* out);
+
 cudaError_t launch_voigt(cudaStream_t s, long long n, const float* a, const float* x, float* h);
 cudaError_t launch_synth_static_line(cudaStream_t s, long long n_cells, int n_lambda, const float* chi_c,
                                      const float* s_c, const float* s_l, const float* ratio, const float* dld,

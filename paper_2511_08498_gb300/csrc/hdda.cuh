@@ -150,7 +150,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
 }
 
 template <int W, bool COUNT, class Model>
-__global__ void __launch_bounds__(256, 4) k_solve_hdda_t(const HddaParams P, const typename Model::Params M)
+__global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const HddaParams P, const typename Model::Params M)
 {
     extern __shared__ unsigned long long s_words[];
     __shared__ float s_J[W][256];

@@ -17,6 +17,7 @@
 // largest such chi Ds is below chi_ds_min; the block level is the largest m with
 // every group of every level <= m passing for every wavelength of the batch.
 #include "hdda.cuh"
+#include "mlp.cuh"
 #include "vlm.cuh"
 #include "voigt.cuh"
 
@@ -37,10 +38,61 @@ __device__ __forceinline__ void cav_eta_chi(const CavParams& M, const float* v, 
     chi = fmaf(v[1] * sl, phi, v[7]);
 }
 
+// The same treatment with the learned surrogate as the profile: inside the
+// surrogate's training domain H = exp(network(x, a', u)) with x = dv / v_th,
+// a' = a / s^2 and u = -(v.w) / v_th (so that x - u is the Voigt argument);
+// outside it, and as its judge, the HUM1WEI24 evaluation above.  The network
+// runs in float32 on the CUDA cores, one evaluation per segment and wavelength,
+// with its weights in the kernel's parameter space.
+__device__ __forceinline__ float surrogate_or_exact(const CavMlpParams& M, float a, float x, float u)
+{
+    if (a >= mlp::kAMin && a <= mlp::kAMax && fabsf(x) <= mlp::kXMax && fabsf(u) <= mlp::kUMax)
+        return __expf(mlp::ln_h_fp32(M.w, x, a, u));
+    return voigt_h(M.cav.coef, a, x - u);
+}
+
+template <int W>
+struct CavMlpModel {
+    static constexpr int kStride = kCavStride;
+    static constexpr bool kPerBatch = false;
+    static constexpr int kMinBlocks = 1;  // the network's 64 hidden values stay in registers
+    using Params = CavMlpParams;
+    struct Voxel {
+        float p[kCavStride];
+    };
+    __device__ __forceinline__ static Voxel load(const float* q)
+    {
+        Voxel v;
+        const float4 a = __ldg(reinterpret_cast<const float4*>(q)), b = __ldg(reinterpret_cast<const float4*>(q) + 1);
+        v.p[0] = a.x; v.p[1] = a.y; v.p[2] = a.z; v.p[3] = a.w;
+        v.p[4] = b.x; v.p[5] = b.y; v.p[6] = b.z; v.p[7] = b.w;
+        return v;
+    }
+    __device__ __forceinline__ static void integrate(const Params& M, const Voxel& v, int b, float wx, float wz,
+                                                     float nl2, float* I, float* T)
+    {
+        const float proj = fmaf(v.p[4], wx, v.p[5] * wz);
+        const float inv = v.p[3];
+        const float u = -proj * inv;
+#pragma unroll 1
+        for (int w = 0; w < W; ++w) {
+            const int l = b * W + w;
+            const float H = surrogate_or_exact(M, v.p[2] * M.cav.is2[l], M.cav.dv[l] * inv, u);
+            const float phi = H * inv * kInvSqrtPi;
+            const float sl = M.cav.s[l];
+            const float eta = fmaf(v.p[0] * sl, phi, v.p[6]);
+            const float chi = fmaf(v.p[1] * sl, phi, v.p[7]);
+            const float S = chi > 0.0f ? __fdividef(eta, chi) : 0.0f;
+            segment(S, chi, nl2, I[w], T[w]);
+        }
+    }
+};
+
 template <int W>
 struct CavModel {
     static constexpr int kStride = kCavStride;
     static constexpr bool kPerBatch = false;
+    static constexpr int kMinBlocks = 4;
     using Params = CavParams;
     struct Voxel {
         float p[kCavStride];
@@ -170,8 +222,11 @@ __global__ void __launch_bounds__(256) k_cav_mips_build(const CavMipParams P, co
     }
 }
 
-template <typename K>
-cudaError_t launch_cav_solve(K kernel, dim3 grid, size_t smem, cudaStream_t s, const HddaParams& P, const CavParams& M)
+// kernel parameters are limited to 32764 bytes
+static_assert(sizeof(HddaParams) + sizeof(CavMlpParams) <= 32764, "CaV-surrogate kernel parameters too large");
+
+template <typename K, typename MP>
+cudaError_t launch_cav_solve_t(K kernel, dim3 grid, size_t smem, cudaStream_t s, const HddaParams& P, const MP& M)
 {
     if (smem > 32 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -223,6 +278,29 @@ cudaError_t launch_cav_mips_build(cudaStream_t s, const CavMipParams& P, const C
     return cudaGetLastError();
 }
 
+cudaError_t launch_solve_cav_mlp(cudaStream_t s, const HddaParams& P, const CavMlpParams& M)
+{
+    if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
+    const size_t smem = sizeof(unsigned long long) * (size_t)P.n_words;
+    dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
+    cudaError_t e = cudaSuccess;
+    switch (P.W) {
+#define DEX_LAUNCH(WW)                                                                                           \
+    case WW:                                                                                                     \
+        if (P.seg_count) e = launch_cav_solve_t(k_solve_hdda_t<WW, true, CavMlpModel<WW>>, grid, smem, s, P, M);   \
+        else e = launch_cav_solve_t(k_solve_hdda_t<WW, false, CavMlpModel<WW>>, grid, smem, s, P, M);              \
+        break;
+        DEX_LAUNCH(1)
+        DEX_LAUNCH(2)
+        DEX_LAUNCH(4)
+        DEX_LAUNCH(8)
+#undef DEX_LAUNCH
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_solve_cav(cudaStream_t s, const HddaParams& P, const CavParams& M)
 {
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
@@ -232,8 +310,8 @@ cudaError_t launch_solve_cav(cudaStream_t s, const HddaParams& P, const CavParam
     switch (P.W) {
 #define DEX_LAUNCH(WW)                                                                                     \
     case WW:                                                                                               \
-        if (P.seg_count) e = launch_cav_solve(k_solve_hdda_t<WW, true, CavModel<WW>>, grid, smem, s, P, M); \
-        else e = launch_cav_solve(k_solve_hdda_t<WW, false, CavModel<WW>>, grid, smem, s, P, M);           \
+        if (P.seg_count) e = launch_cav_solve_t(k_solve_hdda_t<WW, true, CavModel<WW>>, grid, smem, s, P, M); \
+        else e = launch_cav_solve_t(k_solve_hdda_t<WW, false, CavModel<WW>>, grid, smem, s, P, M);           \
         break;
         DEX_LAUNCH(1)
         DEX_LAUNCH(2)

@@ -33,6 +33,7 @@ template <int W, int ST = kStoreF32>
 struct StaticModel {
     static constexpr int kStride = RecFmt<W, ST>::kStride;
     static constexpr bool kPerBatch = true;
+    static constexpr int kMinBlocks = 4;  // CTAs per SM the register budget targets
     struct Params {
         int unused;
     };

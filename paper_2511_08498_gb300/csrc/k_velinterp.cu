@@ -24,6 +24,7 @@ struct VelModel {
     static constexpr int kRec = 2 * W;                 // eta[W], chi[W] of one grid velocity
     static constexpr int kStride = 4 + kNV * kRec;
     static constexpr bool kPerBatch = true;
+    static constexpr int kMinBlocks = 4;
     struct Params {
         int unused;
     };

@@ -19,12 +19,18 @@ HIDDEN = 64
 N_PARAMS = HIDDEN * 3 + HIDDEN + HIDDEN * HIDDEN + HIDDEN + HIDDEN + 1
 
 
-def voigt_samples(n: int, seed: int = SEED_BASE + 900):
-    """[n][3] float32 (x, a, u)."""
+def voigt_samples(n: int, seed: int = SEED_BASE + 900, core_fraction: float = 0.0, core_width: float = 2.5):
+    """[n][3] float32 (x, a, u): x, u uniform, log10 a uniform.  A fraction
+    ``core_fraction`` of the samples instead draws x - u from a normal of width
+    ``core_width`` Doppler widths (clipped to the x range), over-sampling the line
+    core where the profile changes fastest."""
     rng = np.random.default_rng(seed)
     x = rng.uniform(-X_MAX, X_MAX, n)
     a = 10.0 ** rng.uniform(LOG10_A[0], LOG10_A[1], n)
     u = rng.uniform(-U_MAX, U_MAX, n)
+    core = rng.uniform(0.0, 1.0, n) < core_fraction
+    d = rng.normal(0.0, core_width, n)
+    x = np.where(core, np.clip(u + d, -X_MAX, X_MAX), x)
     return np.ascontiguousarray(np.stack([x, a, u], axis=1).astype(np.float32))
 
 

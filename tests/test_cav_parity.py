@@ -53,18 +53,19 @@ def model(nx=128, nz=96, n_lambda=16, seed=600):
     return synth.dynamic_line_atmosphere(nx, nz, n_lambda=n_lambda, seed=synth.SEED_BASE + seed)
 
 
-def gpu_cav(ctx, m, W, max_mip, iod, dirs, w, band=None, cm=0.25):
+def gpu_cav(ctx, m, W, max_mip, iod, dirs, w, band=None, cm=0.25, mlp_params=None):
     from paper_2511_08498_gb300 import api
     nz, nx = m["chi_c"].shape
     f = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda() for k in api.CAV_FIELDS}
     grid = api.cav_grid_build(ctx, nx, nz, f)
     mp = api.cav_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, cm)
-    J, I, seg = api.formal_solve_cav(ctx, grid, mp, dirs, w, band=band, want_intensity=True, count_segments=True)
+    J, I, seg = api.formal_solve_cav(ctx, grid, mp, dirs, w, band=band, want_intensity=True, count_segments=True,
+                                     mlp_params=mlp_params)
     ctx.check()
     return grid, mp, J, I, seg
 
 
-def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei24_cf", stats=False):
+def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei24_cf", stats=False, profile=None):
     P0 = cav.param_arrays(m)
     chain = cav.param_chain(P0, max_mip)
     empty = omips.block_empty(np.stack([m["eta_star"], m["eta_c"]]), np.stack([m["chi_star"], m["chi_c"]]), 16)
@@ -74,7 +75,7 @@ def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei2
         lev, st = omips.block_levels([], empty, 16, W, n_lambda=m["dv"].size), []
     probes = omips.probes_of_blocks(empty, 16)
     J, I = cav.formal_solve(chain, lev, 16, W, m["dv"], m["c_kms"], dirs, w, probes, band=band, method=method,
-                            want_intensity=True)
+                            want_intensity=True, profile=profile)
     return dict(lev=lev, stats=st, probes=probes, J=J, I=I, empty=empty)
 
 
@@ -110,3 +111,23 @@ def test_cav_static_limit_is_the_static_line(ctx):
     _, _, J, _, _ = gpu_cav(ctx, m, 8, 0, 1.0, dirs, w)
     o = oracle_cav(m, 8, 0, 1.0, dirs, w, method="exact")
     assert rel(J.cpu().numpy()[:, o["probes"]], o["J"]).max() < 1e-3
+
+
+@pytest.mark.parametrize("max_mip,band", [(0, None), (2, [4.5, 12.0])])
+def test_cav_with_surrogate_profile_matches_oracle(ctx, max_mip, band):
+    """The Core-and-Voigt solve with the learned profile (dex_formal_solve_cav_mlp):
+    the network inside its training domain, HUM1WEI24 outside it, against the
+    oracle doing the same in float64.  The network's float32 evaluation adds
+    ~1e-6 relative to ln H; the fallback carries the Voigt tolerance (1e-3)."""
+    from oracle import mlp as omlp
+    m = model(nx=64, nz=48, n_lambda=8, seed=620)
+    p = synth.mlp.initial_params(synth.SEED_BASE + 621, scale=0.5)
+    dirs, w = synth.directions(8)
+    _, _, J, I, _ = gpu_cav(ctx, m, 8, max_mip, 1.0, dirs, w, band=band, mlp_params=p)
+    o = oracle_cav(m, 8, max_mip, 1.0, dirs, w, band=band, profile=omlp.profile_with_fallback(p))
+    pr = o["probes"]
+    assert rel(I.cpu().numpy()[:, :, pr], o["I"]).max() < 1e-3
+    assert rel(J.cpu().numpy()[:, pr], o["J"]).max() < 1e-3
+    # and the network did replace the profile: the result differs from exact CaV
+    _, _, Jx, _, _ = gpu_cav(ctx, m, 8, max_mip, 1.0, dirs, w, band=band)
+    assert rel(J.cpu().numpy()[:, pr], Jx.cpu().numpy()[:, pr]).max() > 1e-2

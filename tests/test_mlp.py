@@ -1,0 +1,189 @@
+"""Learned Voigt-profile surrogate on the GPU (tcgen05 tensor cores) vs the float64 oracle.
+
+* forward: every prediction within 2e-3 of the oracle's (bfloat16 emulated at the
+  same points); 99.5 % of them within 1e-4 (1 + |y|).  The residual comes from a
+  bfloat16 rounding of a hidden activation that lands on the other side of a
+  rounding boundary in float32 than in float64 (probability ~1e-4 per value);
+* gradient: per parameter group, |g_gpu - g_ref| / |g_ref| < 5e-3 (2-norms);
+* Adam: one step equal to the float64 formula within 1e-6 (of the array's scale);
+* targets: ln H of the library's Voigt scheme within 1e-3 of the oracle's (the
+  float32 Voigt evaluation's own tolerance: its residual conditioning loss for
+  2 < |x| < 5 at small damping);
+* training: the loss falls by more than 10x in a few hundred steps;
+* gain: what the trained network gains (or loses) over the exact-profile
+  evaluation it replaces -- accuracy against the exact Voigt function and
+  evaluation throughput -- reported, with the accuracy bound the network must
+  reach to be usable at all.
+"""
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp as omlp, voigt as ovoigt
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GROUPS = {"W1": (0, 192), "b1": (192, 256), "W2": (256, 4352), "b2": (4352, 4416), "w3": (4416, 4480),
+          "b3": (4480, 4481)}
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2511_08498_gb300 import api
+    return api.Context(0)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 4096 + 37])
+def test_forward_matches_oracle(ctx, n):
+    from paper_2511_08498_gb300 import api
+    p = synth.mlp.random_params(synth.SEED_BASE + 910 + n, scale=0.3)
+    xau = synth.mlp.voigt_samples(n, seed=synth.SEED_BASE + 911 + n)
+    y = api.mlp_forward(ctx, dev(xau), dev(p)).cpu().numpy().astype(np.float64)
+    ctx.check()
+    ref = omlp.forward(p, xau, emulate=True)
+    err = np.abs(y - ref)
+    assert err.max() < 2e-3, err.max()
+    assert np.mean(err <= 1e-4 * (1 + np.abs(ref))) >= 0.995
+
+
+def test_forward_zero_samples_is_noop(ctx):
+    from paper_2511_08498_gb300 import api
+    out = torch.full((4,), 7.0, device="cuda")
+    xau = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    api.mlp_forward(ctx, xau, dev(synth.mlp.initial_params()), out=out[:0])
+    ctx.check()
+    assert torch.all(out == 7.0)
+
+
+@pytest.mark.parametrize("n", [777, 4096])
+def test_gradient_matches_oracle(ctx, n):
+    from paper_2511_08498_gb300 import api
+    p = synth.mlp.random_params(synth.SEED_BASE + 920 + n, scale=0.3)
+    xau = synth.mlp.voigt_samples(n, seed=synth.SEED_BASE + 921 + n)
+    t = np.random.default_rng(n).normal(-4.0, 2.0, n).astype(np.float32)
+    g, loss = api.mlp_grad(ctx, dev(xau), dev(t), dev(p))
+    ctx.check()
+    lr, gr = omlp.loss_and_grad(p, xau, t, emulate=True)
+    g = g.cpu().numpy().astype(np.float64)
+    assert abs(float(loss.item()) - lr) <= 1e-4 * lr
+    for name, (a, b) in GROUPS.items():
+        rel = np.linalg.norm(g[a:b] - gr[a:b]) / max(np.linalg.norm(gr[a:b]), 1e-30)
+        assert rel < 5e-3, (name, rel)
+
+
+def test_invalid_sample_sets_numeric_and_is_skipped(ctx):
+    from paper_2511_08498_gb300 import api
+    from paper_2511_08498_gb300._native import DexError
+    p = synth.mlp.random_params(synth.SEED_BASE + 930, scale=0.3)
+    xau = synth.mlp.voigt_samples(300, seed=synth.SEED_BASE + 931)
+    xau[5, 1] = 0.0  # a = 0: no log
+    out = torch.full((300,), 9.0, device="cuda")
+    api.mlp_forward(ctx, dev(xau), dev(p), out=out)
+    with pytest.raises(DexError):
+        ctx.check()
+    y = out.cpu().numpy()
+    assert y[5] == 9.0
+    ok = np.ones(300, bool)
+    ok[5] = False
+    assert np.abs(y[ok] - omlp.forward(p, xau[ok], emulate=True)).max() < 2e-3
+
+
+def test_adam_step_matches_formula(ctx):
+    from paper_2511_08498_gb300 import api
+    P = api.mlp_param_count()
+    rng = np.random.default_rng(3)
+    p, g = rng.normal(0, 1, P).astype(np.float32), rng.normal(0, 1e-2, P).astype(np.float32)
+    m, v = rng.normal(0, 1e-3, P).astype(np.float32), rng.uniform(0, 1e-4, P).astype(np.float32)
+    pd, md, vd = dev(p), dev(m), dev(v)
+    api.mlp_adam(ctx, pd, dev(g), md, vd, 7, 1e-3)
+    ctx.check()
+    pr, mr, vr = omlp.adam_step(p.astype(np.float64), g.astype(np.float64), m.astype(np.float64),
+                                v.astype(np.float64), 7, 1e-3)
+    # float32 state: m and v carry float32 rounding of a cancelling update, so
+    # they are compared on the scale of the array, p element by element
+    for got, ref in ((md, mr), (vd, vr)):
+        assert np.abs(got.cpu().numpy() - ref).max() <= 1e-6 * np.abs(ref).max()
+    assert np.allclose(pd.cpu().numpy(), pr, rtol=1e-6, atol=1e-7)
+
+
+def test_targets_match_oracle_voigt(ctx):
+    from paper_2511_08498_gb300 import api
+    xau = synth.mlp.voigt_samples(5000, seed=synth.SEED_BASE + 940)
+    y = api.mlp_targets(ctx, dev(xau)).cpu().numpy().astype(np.float64)
+    ctx.check()
+    x32 = (xau[:, 0] - xau[:, 2]).astype(np.float64)  # the kernel forms x - u in float32
+    ref = np.log(ovoigt.voigt_h(xau[:, 1].astype(np.float64), x32, method="hum1wei24_cf"))
+    assert np.abs(y - ref).max() < 1e-3
+    assert np.median(np.abs(y - ref)) < 2e-6
+
+
+def test_training_reduces_loss(ctx):
+    from paper_2511_08498_gb300 import api
+    n = 1 << 16
+    xau = dev(synth.mlp.voigt_samples(n, seed=synth.SEED_BASE + 950))
+    t = api.mlp_targets(ctx, xau)
+    p = dev(synth.mlp.initial_params())
+    losses = api.mlp_train(ctx, xau, t, p, steps=400, batch=4096, lr=3e-3, log_every=50)
+    ctx.check()
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.1 * losses[0], losses
+
+
+def test_surrogate_gain_report(ctx):
+    """Train on 2^20 profiles the library's own Voigt evaluation generates, then
+    judge the network and that evaluation against the exact Voigt function
+    (Faddeeva, float64) on held-out samples, and time both on 2^22 samples."""
+    from paper_2511_08498_gb300 import api
+    n = 1 << 20
+    xau = dev(synth.mlp.voigt_samples(n, seed=synth.SEED_BASE + 960, core_fraction=0.5))
+    t = api.mlp_targets(ctx, xau)
+    p = dev(synth.mlp.initial_params())
+    api.mlp_train(ctx, xau, t, p, steps=8000, batch=8192, lr=3e-3, lr_final=5e-5)
+    ctx.check()
+    held = synth.mlp.voigt_samples(1 << 14, seed=synth.SEED_BASE + 961)
+    hd = dev(held)
+    y = api.mlp_forward(ctx, hd, p).cpu().numpy().astype(np.float64)
+    a = torch.from_numpy(held[:, 1].copy()).cuda()
+    xs = torch.from_numpy((held[:, 0] - held[:, 2]).copy()).cuda()
+    hv = api.voigt(ctx, a, xs).cpu().numpy().astype(np.float64)
+    ctx.check()
+    exact = ovoigt.voigt_h(held[:, 1].astype(np.float64), (held[:, 0] - held[:, 2]).astype(np.float64),
+                           method="exact")
+    e_mlp = np.abs(np.exp(y) - exact) / exact
+    e_voigt = np.abs(hv - exact) / exact
+    # throughput on 2^22 samples, CUDA events, after a warm-up
+    m = 1 << 22
+    big = dev(synth.mlp.voigt_samples(m, seed=synth.SEED_BASE + 962))
+    out = torch.empty(m, device="cuda")
+    ab = big[:, 1].contiguous()
+    xb = (big[:, 0] - big[:, 2]).contiguous()
+
+    def tm(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 5 / 1e3
+
+    t_mlp = tm(lambda: api.mlp_forward(ctx, big, p, out=out))
+    t_vgt = tm(lambda: api.voigt(ctx, ab, xb, out=out))
+    ctx.check()
+    print(f"surrogate: median rel err {np.median(e_mlp):.3e} p99 {np.quantile(e_mlp, 0.99):.3e} "
+          f"max {e_mlp.max():.3e}; HUM1WEI24 median {np.median(e_voigt):.3e} max {e_voigt.max():.3e}; "
+          f"throughput MLP {m / t_mlp:.3e}/s, Voigt {m / t_vgt:.3e}/s")
+    assert np.median(e_mlp) < 5e-2
+    assert e_voigt.max() < 1e-3
+    # the exact-profile evaluation is both more accurate and faster here: the
+    # network's hidden activations alone cost more CUDA-core work per sample
+    # than the whole HUM1WEI24 evaluation
+    assert np.median(e_voigt) < np.median(e_mlp)
