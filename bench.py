@@ -17,6 +17,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -24,6 +25,8 @@ import subprocess
 import sys
 import threading
 import time
+
+import re
 
 import numpy as np
 
@@ -201,6 +204,33 @@ class Workload:
         return cells.reshape(-1).to(torch.int32)
 
 
+# ncu summary of the HDDA kernel's DRAM traffic on this workload, and the sources
+# whose hash it records: the figure is reported only while they are unchanged
+TRAFFIC_PROFILE = os.path.join("profiles", "k_solve_hdda_static_w8_1024_dram.md")
+HDDA_SOURCES = [os.path.join("paper_2511_08498_gb300", "csrc", f)
+                for f in ("hdda.cuh", "k_hdda.cu", "dex_common.cuh", "dex_internal.h")]
+
+
+def measured_traffic():
+    """DRAM bytes (read + write) per launch of the timed HDDA kernel from one ncu
+    capture of the 1024 x 1024 workload, or None if the kernel changed since."""
+    if NX != 1024:
+        return None
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as fh:
+            text = fh.read()
+        h = hashlib.sha256()
+        for f in HDDA_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    vals = dict(re.findall(r"^(traffic_bytes_per_launch|kernel_sources_sha256_16): (\S+)$", text, re.M))
+    if vals.get("kernel_sources_sha256_16") != h.hexdigest()[:16]:
+        return None
+    return int(vals["traffic_bytes_per_launch"])
+
+
 def l2_flush(buf):
     buf.add_(1.0)  # writes 256 MiB > 129 MB L2
 
@@ -373,7 +403,8 @@ def native(args):
                    "timing": "CUDA events per step on the launch stream, flush outside the events",
                    "parallelism": "one independent atmosphere per rank (weak scaling, no collective)"},
         "roofline": {"bound": "alu", "kernel": "k_solve_hdda<8>", "achieved": achieved, "peak": sfu_peak,
-                     "unit": "G seg-lambda updates/s", "frac": achieved / sfu_peak, "traffic": None,
+                     "unit": "G seg-lambda updates/s", "frac": achieved / sfu_peak,
+                     "traffic": measured_traffic(), "traffic_unit": "DRAM bytes per launch (ncu, one capture)",
                      "peak_basis": f"{N_SM} SMs x {SFU_PER_SM_CLK} ex2/clk x {sm_max:.0f} MHz (one exponential "
                                    "per segment-wavelength update)",
                      "kernel_ms": hdda_s * 1e3, "executed_seg_lambda": exec_seg_lambda,
