@@ -314,12 +314,9 @@ def native(args):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    step_s = sum(times) / 1e3
-    if world > 1:
-        t = torch.tensor([step_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_s = float(t.item())
-    total_units = dense_seg_lambda * args.steps * world
+    from paper_2511_08498_gb300.distributed import reduce_scalar
+    step_s = reduce_scalar(sum(times) / 1e3, "max")            # the slowest rank's time
+    total_units = reduce_scalar(dense_seg_lambda * args.steps, "sum")  # every rank's atmosphere
     value = total_units / step_s
     ms_per_step = step_s * 1e3 / args.steps
     hdda_s = sum(hdda_times) / 1e3 / args.steps

@@ -40,11 +40,12 @@ def _time(fn, reps=5):
     return e0.elapsed_time(e1) / reps / 1e3
 
 
-def train(ctx, log2_samples=24, steps=20000, batch=16384, lr=3e-3, lr_final=3e-5, seed_offset=0):
+def train(ctx, log2_samples=24, steps=20000, batch=16384, lr=3e-3, lr_final=3e-5, seed_offset=0,
+          core_fraction=0.5):
     import synth
     n = 1 << log2_samples
     xau = torch.from_numpy(synth.mlp.voigt_samples(n, seed=synth.SEED_BASE + 970 + seed_offset,
-                                                   core_fraction=0.5)).cuda()
+                                                   core_fraction=core_fraction)).cuda()
     target = api.mlp_targets(ctx, xau)
     params = torch.from_numpy(synth.mlp.initial_params()).cuda()
     t0 = time.time()
@@ -104,13 +105,21 @@ def main(argv=None):
     ap.add_argument("--log2-samples", type=int, default=24)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--lr", type=float, default=3e-3)
+    ap.add_argument("--lr-final", type=float, default=3e-5)
+    ap.add_argument("--core-fraction", type=float, default=0.5)
     ap.add_argument("--out", default=None)
     ap.add_argument("--no-cav", action="store_true")
+    ap.add_argument("--save", default=None, help="write the trained parameters (.npy)")
     args = ap.parse_args(argv)
     ctx = api.Context(0)
-    params, losses, secs = train(ctx, args.log2_samples, args.steps, args.batch)
-    rep = {"samples": 1 << args.log2_samples, "steps": args.steps, "batch": args.batch, "train_seconds": secs,
+    params, losses, secs = train(ctx, args.log2_samples, args.steps, args.batch, args.lr, args.lr_final,
+                                 core_fraction=args.core_fraction)
+    rep = {"samples": 1 << args.log2_samples, "steps": args.steps, "batch": args.batch, "lr": args.lr,
+           "lr_final": args.lr_final, "core_fraction": args.core_fraction, "train_seconds": secs,
            "loss_curve": losses}
+    if args.save:
+        np.save(args.save, params.cpu().numpy())
     rep.update(judge(ctx, params))
     if not args.no_cav:
         rep["cav"] = cav_compare(ctx, params)
