@@ -103,8 +103,8 @@ def cav_compare(ctx, params, nx=256, nz=128, n_lambda=64, n_dir=64, max_mip=3, b
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--log2-samples", type=int, default=24)
-    ap.add_argument("--steps", type=int, default=20000)
-    ap.add_argument("--batch", type=int, default=16384)
+    ap.add_argument("--steps", type=int, default=40000)
+    ap.add_argument("--batch", type=int, default=32768)
     ap.add_argument("--lr", type=float, default=3e-3)
     ap.add_argument("--lr-final", type=float, default=3e-5)
     ap.add_argument("--core-fraction", type=float, default=0.5)

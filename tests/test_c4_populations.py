@@ -1,0 +1,73 @@
+"""Population error of the accelerated path against the float64 oracle (the
+paper's error measure, Section 4.1: level populations after the iteration).
+
+Workload: the three-level-atom population model at 128 x 128 (the reduced
+instance of the 2048 x 2048 configuration: same generators, 96 wavelengths,
+96 directions, 20 Lambda steps from LTE).  The float64 oracle's populations are
+stored in tests/golden/populations_128.npz, written by
+``python -m oracle.populations_ref --n 128``.
+
+Bars: the plain float32 path within 1e-3 of the oracle everywhere; the
+accelerated path (VLM levels 0-3, IoD 1e-2, distance limits) with float32 or
+scaled-float16 bricks within 0.5 % at the 99.9th percentile; bfloat16 bricks
+are reported (their 8-bit significand is known to miss the bar).
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from synth.atom import line_wavelength_grid, populations_atmosphere, three_level_atom
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "populations_128.npz")
+N = 128
+BAND = [6.0, 24.0, 96.0]
+
+
+@pytest.fixture(scope="module")
+def case():
+    from paper_2511_08498_gb300 import api
+    g = np.load(GOLDEN)
+    assert int(g["n"]) == N
+    ad = three_level_atom()
+    m = populations_atmosphere(N, N, seed=synth.SEED_BASE + 4)
+    lam, tag = line_wavelength_grid()
+    dirs, w = synth.directions(int(g["n_dir"]))
+    atom = api.Atom.from_dict(ad, m["cell_cm"])
+    dev = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda() for k in ("temperature", "ne", "nh")}
+    live = m["temperature"].reshape(-1) > 0
+    return dict(api=api, ctx=api.Context(0), ref=g["populations"], n_iter=int(g["n_iter"]), atom=atom, lam=lam,
+                tag=tag, dirs=dirs, w=w, dev=dev, live=live)
+
+
+def run(c, accelerated, storage=0):
+    d = c["dev"]
+    p = c["api"].lambda_iteration(c["ctx"], c["atom"], c["lam"], c["tag"], d["temperature"], d["ne"], d["nh"], N, N,
+                                  c["dirs"], c["w"], c["n_iter"], accelerated=accelerated, iod=1e-2, band=BAND,
+                                  storage=storage)
+    c["ctx"].check()
+    return p.cpu().numpy()
+
+
+def err_pct(c, p):
+    e = np.abs(p - c["ref"]) / np.maximum(np.abs(c["ref"]), 1e-300)
+    e = e[:, c["live"]].reshape(-1) * 100.0
+    return {q: float(np.percentile(e, v)) for q, v in (("p50", 50), ("p99", 99), ("p99.9", 99.9), ("max", 100))}
+
+
+def test_plain_path_matches_oracle(case):
+    e = err_pct(case, run(case, False))
+    print("plain", e)
+    assert e["max"] < 0.1
+
+
+@pytest.mark.parametrize("storage,bar", [(0, 0.5), (2, 0.5), (1, 5.0)])
+def test_accelerated_population_error(case, storage, bar):
+    e = err_pct(case, run(case, True, storage))
+    print(["f32", "bf16", "f16"][storage], e)
+    assert e["p99.9"] < bar
