@@ -54,10 +54,9 @@ WORKLOAD = (f"sparse static-line atmosphere {NX}x{NZ}, 16^2 blocks, 40% empty, {
 VARIANTS = [("strict_iod_1e-3", THR_STRICT, BAND, 0), ("paper_iod_1", 1.0, BAND, 0),
             ("unlimited_vlm", 1e30, BAND, 0), ("no_distance_limit_iod_1e-2", THR, None, 0),
             ("bf16_bricks", THR, BAND, 1), ("f16_bricks", THR, BAND, 2)]
-# SM count x SFU ex2 results per clock per SM x max SM clock: each segment-wavelength
-# update needs one exponential, so this bounds the updates per second
-SFU_PER_SM_CLK = 16
-N_SM = 152
+# Each segment-wavelength update needs one 2^x on the special-function units, so
+# their measured 2^x throughput (dex_measure_ex2_rate, ~30 per SM per clock on a
+# GB300 at 2070 MHz) bounds the updates per second of the solve kernels.
 
 
 def parse():
@@ -207,8 +206,9 @@ class Workload:
 # ncu summary of the HDDA kernel's DRAM traffic on this workload, and the sources
 # whose hash it records: the figure is reported only while they are unchanged
 TRAFFIC_PROFILE = os.path.join("profiles", "k_solve_hdda_static_w8_1024_dram.md")
-HDDA_SOURCES = [os.path.join("paper_2511_08498_gb300", "csrc", f)
-                for f in ("hdda.cuh", "k_hdda.cu", "dex_common.cuh", "dex_internal.h")]
+HDDA_SOURCES = [os.path.join("paper_2511_08498_gb300", "csrc", f) for f in ("hdda.cuh", "k_hdda.cu", "dex_common.cuh")]
+# ... and, from the internal header, the kernel's parameter structs
+HDDA_STRUCTS = (os.path.join("paper_2511_08498_gb300", "csrc", "dex_internal.h"), ("HddaParams",))
 
 
 def measured_traffic():
@@ -223,6 +223,11 @@ def measured_traffic():
         for f in HDDA_SOURCES:
             with open(os.path.join(ROOT, f), "rb") as fh:
                 h.update(fh.read())
+        with open(os.path.join(ROOT, HDDA_STRUCTS[0])) as fh:
+            header = fh.read()
+        for name in HDDA_STRUCTS[1]:
+            m = re.search(r"^struct " + name + r" \{.*?^\};", header, re.S | re.M)
+            h.update((m.group(0) if m else "").encode())
     except OSError:
         return None
     vals = dict(re.findall(r"^(traffic_bytes_per_launch|kernel_sources_sha256_16): (\S+)$", text, re.M))
@@ -262,6 +267,9 @@ def native(args):
     torch.cuda.set_device(local)
     from paper_2511_08498_gb300 import api
     ctx = api.Context(local)
+    ex2_rate = api.measure_ex2_rate(ctx)  # the roofline's ceiling, measured on this GPU
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_clock_mhz = float(measured_peaks()[0].get("sm_max_mhz", 2070.0))
     wl = Workload(ctx, seed_offset=rank)
     flush_buf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
@@ -378,8 +386,7 @@ def native(args):
     ctx.check()
 
     peaks, peak_src = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    sfu_peak = N_SM * SFU_PER_SM_CLK * sm_max * 1e6 / 1e9  # G updates / s
+    sfu_peak = ex2_rate / 1e9  # G updates / s, measured before the timed region
     achieved = exec_seg_lambda / hdda_s / 1e9
     plain_achieved = dense_seg_lambda / plain_kern_s / 1e9
     out = {
@@ -402,8 +409,10 @@ def native(args):
         "roofline": {"bound": "alu", "kernel": "k_solve_hdda<8>", "achieved": achieved, "peak": sfu_peak,
                      "unit": "G seg-lambda updates/s", "frac": achieved / sfu_peak,
                      "traffic": measured_traffic(), "traffic_unit": "DRAM bytes per launch (ncu, one capture)",
-                     "peak_basis": f"{N_SM} SMs x {SFU_PER_SM_CLK} ex2/clk x {sm_max:.0f} MHz (one exponential "
-                                   "per segment-wavelength update)",
+                     "peak_basis": "measured 2^x throughput of the special-function units "
+                                   "(dex_measure_ex2_rate: 8 independent ex2.approx chains per thread, 8 CTAs/SM); "
+                                   "one exponential per segment-wavelength update",
+                     "peak_ex2_per_sm_clk": ex2_rate / n_sm / (sm_clock_mhz * 1e6),
                      "kernel_ms": hdda_s * 1e3, "executed_seg_lambda": exec_seg_lambda,
                      "hbm_algorithmic_gbs": exec_seg_lambda * 8 / hdda_s / 1e9,
                      "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "peak_source": peak_src},

@@ -483,6 +483,14 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
 int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, int ctas,
                             unsigned long long* done_ns, unsigned long long* start_ns);
 
+/* Measured throughput (operations per second) of the special-function unit's
+ * 2^x (ex2.approx.ftz.f32) on the context's device: every segment-wavelength
+ * update of the solvers needs one, so this is the ceiling their update rate is
+ * reported against.  Runs a short probe kernel (8 x SMs CTAs, ~1 ms) on the
+ * context's stream and synchronises it; allocates and frees 1.2 MB of device
+ * memory.  No paper counterpart (a measurement utility). */
+int dex_measure_ex2_rate(dex_ctx* ctx, double* ops_per_s);
+
 /* ------------------------------------------------------------------------
  * Learned Voigt-profile surrogate.  The paper evaluates the Voigt profile of
  * the Core-and-Voigt treatment on the fly (Section 3.2); this library adds a

@@ -584,6 +584,13 @@ def batch_solve_noalloc(ctx: Context, items, W: int, ctas: int = 0, done_ns: tor
     ctx._rc(lib().dex_batch_solve_noalloc(ctx.handle, len(items), arr, W, int(ctas), _ptr(done_ns), _ptr(start_ns)))
 
 
+def measure_ex2_rate(ctx: Context) -> float:
+    """Measured 2^x throughput of the special-function units (``dex_measure_ex2_rate``), per second."""
+    v = ctypes.c_double(0.0)
+    ctx._rc(lib().dex_measure_ex2_rate(ctx.handle, ctypes.byref(v)))
+    return float(v.value)
+
+
 # ------------------------------------------------------ profile surrogate --
 
 def mlp_param_count() -> int:

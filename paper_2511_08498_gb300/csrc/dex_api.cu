@@ -964,3 +964,14 @@ int dex_mlp_targets(dex_ctx* ctx, long long n, const float* xau, float* out)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp targets launch");
     return ok(ctx);
 }
+
+// ---------------------------------------------------------- measurement --
+int dex_measure_ex2_rate(dex_ctx* ctx, double* ops_per_s)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (!ops_per_s) return fail(ctx, DEX_ERR_ARG, "null output");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::measure_ex2_rate(ctx->stream, ops_per_s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ex2 rate probe");
+    return ok(ctx);
+}

@@ -156,6 +156,9 @@ cudaError_t noalloc_scratch(unsigned int** out);
 
 int chain_length(int max_mip);
 int record_floats(int W, int storage);
+// special-function-unit 2^x throughput (k_probe.cu); synchronises the stream
+cudaError_t measure_ex2_rate(cudaStream_t s, double* ops_per_s);
+
 // learned profile surrogate (k_mlp.cu)
 struct MlpParams {
     long long n;                 // samples

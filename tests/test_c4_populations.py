@@ -45,10 +45,10 @@ def case():
                 tag=tag, dirs=dirs, w=w, dev=dev, live=live)
 
 
-def run(c, accelerated, storage=0):
+def run(c, accelerated, storage=0, iod=1e-2):
     d = c["dev"]
     p = c["api"].lambda_iteration(c["ctx"], c["atom"], c["lam"], c["tag"], d["temperature"], d["ne"], d["nh"], N, N,
-                                  c["dirs"], c["w"], c["n_iter"], accelerated=accelerated, iod=1e-2, band=BAND,
+                                  c["dirs"], c["w"], c["n_iter"], accelerated=accelerated, iod=iod, band=BAND,
                                   storage=storage)
     c["ctx"].check()
     return p.cpu().numpy()
@@ -66,8 +66,9 @@ def test_plain_path_matches_oracle(case):
     assert e["max"] < 0.1
 
 
-@pytest.mark.parametrize("storage,bar", [(0, 0.5), (2, 0.5), (1, 5.0)])
-def test_accelerated_population_error(case, storage, bar):
-    e = err_pct(case, run(case, True, storage))
-    print(["f32", "bf16", "f16"][storage], e)
+@pytest.mark.parametrize("iod,storage,bar", [(1e-2, 0, 0.5), (1e-2, 2, 0.5), (1e-2, 1, 5.0),
+                                             (1.0, 0, 50.0), (1.0, 2, 50.0), (1.0, 1, 50.0), (1e30, 0, 50.0)])
+def test_accelerated_population_error(case, iod, storage, bar):
+    e = err_pct(case, run(case, True, storage, iod))
+    print(f"iod {iod:g}", ["f32", "bf16", "f16"][storage], e)
     assert e["p99.9"] < bar
