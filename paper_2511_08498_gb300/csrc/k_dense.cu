@@ -112,7 +112,10 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
             const bool on_x = tnx <= tnz;
             const float th = on_x ? tnx : tnz;
             const float tl = plane_lo(on_x ? Px : Pz, on_x ? ax : az, th);
-            const float len = (th - th_prev) + (tl - tl_prev);
+            // where an x and a z plane share the rounded parameter (a corner), the lo
+            // parts order them and the zero-length step between them can come out a
+            // few ulps negative: clamped, or e^{-chi len} overflows in thick cells
+            const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
             if (it >= cap || (unsigned)ci >= (unsigned)P.nx || (unsigned)cj >= (unsigned)P.nz) {
                 capped = true;
                 break;

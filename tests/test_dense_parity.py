@@ -128,3 +128,31 @@ def test_argument_errors_enqueue_nothing(ctx):
     with pytest.raises(DexError):
         api.formal_solve_dense(ctx, 4, 4, 1, 1, planes, [[1, 1]], [1.0])  # not a unit vector
     ctx.check()
+
+
+@pytest.mark.parametrize("solver", ["dense", "hdda"])
+def test_optically_thick_uniform_slab_full_size(ctx, solver):
+    """1024 x 1024 uniform slab, opacities 1e2 .. 1e9 per cell, 96 directions:
+    every ray saturates, so I = S (1 - e^{-tau}) = S and J = S at every cell
+    (closed form).  Large grids and many directions put x and z plane crossings
+    on the same rounded parameter; the zero-length step between them must not
+    come out negative, which here would turn e^{-chi len} into an overflow and
+    J into NaN."""
+    from paper_2511_08498_gb300 import api
+    n, L = 1024, 8
+    S = 1.0 + 0.25 * np.arange(L, dtype=np.float32)
+    chi = np.broadcast_to((10.0 ** np.arange(2, 2 + L, dtype=np.float32))[:, None], (L, n * n)).copy()
+    eta = (chi * S[:, None]).astype(np.float32)
+    dirs, w = synth.directions(96)
+    e, c = torch.from_numpy(eta).cuda(), torch.from_numpy(chi).cuda()
+    if solver == "dense":
+        planes = api.pack_planes(ctx, e, c, 8)
+        J, _, _ = api.formal_solve_dense(ctx, n, n, L, 8, planes, dirs, w)
+    else:
+        grid = api.grid_build(ctx, n, n, e, c)
+        mips = api.mips_build(ctx, grid, e, c, 8, 0, 1.0, 1.0, 0.25)
+        J, _, _ = api.formal_solve_hdda(ctx, grid, mips, dirs, w)
+    ctx.check()
+    J = J.cpu().numpy().astype(np.float64)
+    assert np.isfinite(J).all()
+    assert np.abs(J / S[:, None].astype(np.float64) - 1.0).max() < 1e-5
