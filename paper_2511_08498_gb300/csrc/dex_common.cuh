@@ -107,6 +107,17 @@ __device__ __forceinline__ void segment2(float2 S, float2 chi, float nl2, float&
     T1 = T.y;
 }
 
+// True when every transmission is exactly zero (underflowed): from then on each
+// update adds T S (1 - e) = 0 and keeps T = 0, so the rest of the ray changes nothing.
+template <int W>
+__device__ __forceinline__ bool all_opaque(const float* T)
+{
+    unsigned int bits = 0u;
+#pragma unroll
+    for (int w = 0; w < W; ++w) bits |= __float_as_uint(T[w]);
+    return bits == 0u;
+}
+
 // All W wavelengths of a record: pairs on the packed pipe, an odd one alone.
 template <int W>
 __device__ __forceinline__ void segments(const float* S, const float* chi, float nl2, float* I, float* T)

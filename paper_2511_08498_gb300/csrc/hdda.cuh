@@ -94,6 +94,10 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
                 rp += negz ? -side * REC : side * REC;
                 cross = (unsigned)lz >= (unsigned)side;
             }
+            // early termination, checked where the ray enters another block: once every
+            // transmission has underflowed to exactly zero the rest of the ray adds
+            // exact zeros, so stopping leaves I and T bit-identical
+            if (cross && all_opaque<W>(T)) break;
             if (cross) {  // entered another block
                 const int bxn = bxc + (on_x ? sx : 0), bzn = bzc + (on_x ? 0 : sz);
                 if ((unsigned)bxn >= (unsigned)G.nbx || (unsigned)bzn >= (unsigned)G.nbz) {

@@ -49,6 +49,22 @@ def _err(J, ref):
             "max": float(e.max())}
 
 
+def dense_seg_lambda(ctx, grid, n_lambda, W, dirs, w):
+    """Full-resolution segment-wavelengths of every probe (every cell of every
+    non-empty block) over all directions: the plain solver's counting pass, which
+    walks every cell whatever the medium (zero planes suffice)."""
+    act = torch.nonzero(grid.block_offset >= 0).reshape(-1)
+    bx, bz = act % grid.nbx, act // grid.nbx
+    loc = torch.arange(256, device=act.device)
+    cells = ((bz[:, None] * 16 + loc[None, :] // 16) * grid.nx + bx[:, None] * 16 + loc[None, :] % 16)
+    cells = cells.reshape(-1).to(torch.int32)
+    planes = torch.zeros((1, grid.nx * grid.nz, 2 * W), device="cuda")
+    _, _, seg = api.formal_solve_dense(ctx, grid.nx, grid.nz, W, W, planes, dirs, w, probes=cells,
+                                       count_segments=True)
+    ctx.check()
+    return int(seg.item()) * -(-n_lambda // W) * W
+
+
 def report(nx=2048, nz=1024, n_lambda=64, n_dir=64, W=8, max_mip=3, iod=1e-2, mlp_params=None, mlp_nx=256,
            mlp_nz=128, reps=2):
     import synth
@@ -60,9 +76,7 @@ def report(nx=2048, nz=1024, n_lambda=64, n_dir=64, W=8, max_mip=3, iod=1e-2, ml
     n_cells = nx * nz
     ref = torch.empty((n_lambda, n_cells), device="cuda")
     plain = api.cav_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, 0, iod, iod, 0.25)
-    _, _, seg = api.formal_solve_cav(ctx, grid, plain, dirs, w, J=ref, count_segments=True)
-    ctx.check()
-    dense = int(seg.item()) * W
+    dense = dense_seg_lambda(ctx, grid, n_lambda, W, dirs, w)
     t_plain = _time(lambda: api.formal_solve_cav(ctx, grid, plain, dirs, w, J=ref), reps)
     out = {"workload": f"moving-medium atmosphere {nx}x{nz}, {n_lambda} wavelengths, {n_dir} directions, "
                        f"W={W}, VLM mip 0-{max_mip}, IoD {iod:g}, distance limits {BAND}",
