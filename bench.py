@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-populations", action="store_true", help="skip the population-error check")
     ap.add_argument("--nx", type=int, default=1024, help="grid side (smaller sides for profiling captures)")
     ap.add_argument("--phase", default="all", choices=["all", "accel", "plain"],
                     help="accel/plain: time only that path (profiling captures)")
@@ -426,7 +427,7 @@ def native(args):
         "executed_fraction": exec_seg_lambda / dense_seg_lambda,
         "j_err_pct_vs_plain": err_pct(acc_probe),
         "error_measure": "relative J error (%) at every probe and wavelength vs the plain FP32 GPU solve "
-                         "(itself within 1e-5 of the FP64 oracle); populations: see the Lambda-iteration report",
+                         "(itself within 1e-5 of the FP64 oracle); population error: see 'populations'",
         "variants": variants,
         "mip_level_fraction": level_frac,
         "e2e": {"value": dense_seg_lambda * args.steps / e2e_s, "unit": "seg-lambda/s",
@@ -434,12 +435,58 @@ def native(args):
         "gpu_launches": wl.launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    if not args.no_populations and args.phase == "all":
+        out["populations"] = population_check(ctx, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, probes.cpu().numpy())
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------ population check --
+
+POP_N, POP_ITERS, POP_DIRS = 1024, 20, 96
+
+
+def population_check(ctx, torch):
+    """The metric's error qualifier on the workload it is defined on: the
+    three-level-atom Lambda iteration (1024 x 1024, 96 wavelengths, 96
+    directions, 20 steps from LTE) with the plain and the accelerated solve
+    (VLM 0-3, unlimited averaging and IoD 1e-2, distance limits); time per
+    iteration and population error of the accelerated run vs the plain one."""
+    import synth
+    from paper_2511_08498_gb300 import api
+    from synth.atom import line_wavelength_grid, populations_atmosphere, three_level_atom
+    m = populations_atmosphere(POP_N, POP_N, seed=synth.SEED_BASE + 4)
+    lam, tag = line_wavelength_grid()
+    dirs, w = synth.directions(POP_DIRS)
+    atom = api.Atom.from_dict(three_level_atom(), m["cell_cm"])
+    dev = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda() for k in ("temperature", "ne", "nh")}
+    live = torch.from_numpy(m["temperature"].reshape(-1) > 0).cuda()
+
+    def run(accelerated, iod):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p = api.lambda_iteration(ctx, atom, lam, tag, dev["temperature"], dev["ne"], dev["nh"], POP_N, POP_N,
+                                 dirs, w, POP_ITERS, accelerated=accelerated, iod=iod, band=BAND)
+        e1.record()
+        e1.synchronize()
+        ctx.check()
+        return p, e0.elapsed_time(e1) / 1e3 / POP_ITERS
+
+    ref, t_plain = run(False, THR)
+    out = {"workload": f"three-level atom {POP_N}x{POP_N}, {lam.size} wavelengths, {POP_DIRS} directions, "
+                       f"{POP_ITERS} Lambda steps from LTE", "plain_s_per_iteration": t_plain}
+    for name, iod in (("iod_1e-2", THR), ("unlimited_vlm", 1e30)):
+        p, t = run(True, iod)
+        e = ((p - ref).abs() / ref.abs().clamp_min(1e-300))[:, live].reshape(-1).double().cpu().numpy() * 100.0
+        out[name] = {"s_per_iteration": t, "speedup_vs_plain": t_plain / t,
+                     "pop_err_pct_vs_plain": {q: float(np.percentile(e, v)) for q, v in
+                                              (("p50", 50), ("p99", 99), ("p99.9", 99.9), ("max", 100))}}
+    return out
 
 
 # --------------------------------------------------------- oracle on CPU --
