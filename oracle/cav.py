@@ -8,7 +8,7 @@ Model (one line plus an isotropic background, velocities and wavelengths in km/s
   s = lambda0 / lambda = 1 / (1 + dv / c)
   eta = eta* s phi + eta_c,  chi = chi* s phi + chi_c,          (eta*(lambda) = (lambda0/lambda) eta*(lambda0))
   phi = H(a / s^2, u / v_th) / (sqrt(pi) v_th)                  (a(lambda) = (lambda/lambda0)^2 a(lambda0))
-with H the Voigt function: the exact Faddeeva value for the "exact" judge, or
+with H the Voigt function: the exact Faddeeva value (method "exact", the accuracy reference), or
 HUM1WEI24 (the form the method evaluates) for parity with the GPU.
 
 Acceleration (restated from Section 3.2 and Section 2.2):

@@ -8,7 +8,7 @@ on a seeded stratified atmosphere; the formal solution is the plain float64
 long-characteristics oracle at full resolution from every cell of every
 non-empty block.  Everything in float64 (no float32 rounding of the
 emissivity/opacity), so the stored populations are the reference the GPU's
-float32 path and its reduced-precision storage are judged against.
+float32 path and its reduced-precision storage are compared with.
 
 Usage: python -m oracle.populations_ref [--n 128] [--out tests/golden/populations_128.npz]
 """

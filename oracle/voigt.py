@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU-baseline leg).
 
-* ``exact``: the Faddeeva function from scipy (``scipy.special.wofz``): the judge.
+* ``exact``: the Faddeeva function from scipy (``scipy.special.wofz``): the accuracy reference.
 * ``hum1wei24``: the approximation Section 3.2 names (Schreier 2018, "HUM1WEI24"),
   restated from its published sources, in float64 (``method="hum1wei24"``):
     - |x| + y >= 15: region I of Humlicek (1982), w(z) = i z / (sqrt(pi) (z^2 - 1/2));

@@ -41,7 +41,7 @@ __device__ __forceinline__ void cav_eta_chi(const CavParams& M, const float* v, 
 // The same treatment with the learned surrogate as the profile: inside the
 // surrogate's training domain H = exp(network(x, a', u)) with x = dv / v_th,
 // a' = a / s^2 and u = -(v.w) / v_th (so that x - u is the Voigt argument);
-// outside it, and as its judge, the HUM1WEI24 evaluation above.  The network
+// outside it, and as its accuracy reference, the HUM1WEI24 evaluation above.  The network
 // runs in float32 on the CUDA cores, one evaluation per segment and wavelength,
 // with its weights in the kernel's parameter space.
 __device__ __forceinline__ float surrogate_or_exact(const CavMlpParams& M, float a, float x, float u)

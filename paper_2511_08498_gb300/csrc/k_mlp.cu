@@ -3,7 +3,7 @@
 // wavelength offset x (Doppler widths, rest frame), the damping a and the
 // projected velocity u (Doppler widths).  It stands in for the on-the-fly
 // profile evaluation of the Core-and-Voigt treatment (Section 3.2); the exact
-// HUM1WEI24 evaluation remains the fallback and the error judge.
+// HUM1WEI24 evaluation remains the fallback and the accuracy reference.
 //
 // Precision: weights are used as BF16 (rounded from an FP32 master copy), the
 // hidden activations that feed the tensor cores are BF16, every sum is FP32.

@@ -5,7 +5,7 @@ Steps (each a library call; this module only sequences them):
      half of them concentrated on the line core (synth.mlp.voigt_samples);
   2. targets ln H(a, x - u) from the library's own Voigt evaluation (dex_mlp_targets);
   3. minibatch Adam on the tensor-core gradient kernel (dex_mlp_grad, dex_mlp_adam);
-  4. judge on held-out uniform samples against the same exact-profile evaluation:
+  4. evaluate on held-out uniform samples against the same exact-profile evaluation:
      relative error of H, and evaluation throughput of the network (tcgen05
      inference, dex_mlp_forward) against the Voigt kernel (dex_voigt);
   5. the Core-and-Voigt solve of a moving-medium atmosphere with the exact
@@ -55,7 +55,7 @@ def train(ctx, log2_samples=24, steps=20000, batch=16384, lr=3e-3, lr_final=3e-5
     return params, losses, time.time() - t0
 
 
-def judge(ctx, params, n_held=1 << 16, n_time=1 << 22):
+def evaluate(ctx, params, n_held=1 << 16, n_time=1 << 22):
     import synth
     held = torch.from_numpy(synth.mlp.voigt_samples(n_held, seed=synth.SEED_BASE + 980)).cuda()
     y = api.mlp_forward(ctx, held, params)
@@ -120,7 +120,7 @@ def main(argv=None):
            "loss_curve": losses}
     if args.save:
         np.save(args.save, params.cpu().numpy())
-    rep.update(judge(ctx, params))
+    rep.update(evaluate(ctx, params))
     if not args.no_cav:
         rep["cav"] = cav_compare(ctx, params)
     s = json.dumps(rep)

@@ -1,0 +1,33 @@
+"""Shared test helper: which block levels sit safely away from the VLM thresholds."""
+
+import numpy as np
+
+
+def robust_level_mask(stats, level_map, lambda_batch, block, max_mip, te, tc, cm, eps=1e-4):
+    """True where the oracle's block level is not within eps of any deciding threshold."""
+    n_batch, nbz, nbx = level_map.shape
+    rp, rf = [], []
+    for st in stats:
+        L = st["iod_eta"].shape[0]
+        with np.errstate(invalid="ignore"):
+            p = ((st["iod_eta"] < te * (1 - eps)) & (st["iod_chi"] < tc * (1 - eps))) | (st["chi_ds"] < cm * (1 - eps))
+            f = ((st["iod_eta"] > te * (1 + eps)) | (st["iod_chi"] > tc * (1 + eps))) & (st["chi_ds"] > cm * (1 + eps))
+        side = p.shape[1] // nbz
+
+        def per_batch(a, red):
+            blk = red(a.reshape(L, nbz, side, nbx, side), axis=(2, 4))
+            return np.stack([red(blk[b * lambda_batch:(b + 1) * lambda_batch], axis=0) for b in range(n_batch)])
+        rp.append(per_batch(p, np.all))
+        rf.append(per_batch(f, np.any))
+    ok = np.ones(level_map.shape, dtype=bool)
+    for b in range(n_batch):
+        for bz in range(nbz):
+            for bx in range(nbx):
+                L_ = level_map[b, bz, bx]
+                if L_ < 0:
+                    continue
+                good = all(rp[m - 1][b, bz, bx] for m in range(1, L_ + 1))
+                if L_ < max_mip:
+                    good = good and rf[L_][b, bz, bx]
+                ok[b, bz, bx] = good
+    return ok

@@ -137,7 +137,7 @@ def test_training_reduces_loss(ctx):
 
 def test_surrogate_gain_report(ctx):
     """Train on 2^20 profiles the library's own Voigt evaluation generates, then
-    judge the network and that evaluation against the exact Voigt function
+    compare the network and that evaluation with the exact Voigt function
     (Faddeeva, float64) on held-out samples, and time both on 2^22 samples."""
     from paper_2511_08498_gb300 import api
     n = 1 << 20
