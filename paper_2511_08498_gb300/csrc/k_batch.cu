@@ -32,7 +32,6 @@ __device__ __forceinline__ unsigned long long global_ns()
 template <int W>
 struct StaticRec {
     static constexpr int kStride = 2 * W;
-    static constexpr bool kPerBatch = true;
     struct Params {
         int unused;
     };
