@@ -491,6 +491,12 @@ int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms,
  * memory.  No paper counterpart (a measurement utility). */
 int dex_measure_ex2_rate(dex_ctx* ctx, double* ops_per_s);
 
+/* Self-test of the device-side failure path: one thread waits on an mbarrier
+ * that nothing arrives on, with the same bounded wait the tensor-core kernels
+ * use, giving up after `polls` (1 .. 1e6) polls; the next dex_ctx_check then
+ * returns DEX_ERR_TIMEOUT and the context stays usable.  No fault, no hang. */
+int dex_selftest_wait_timeout(dex_ctx* ctx, int polls);
+
 /* ------------------------------------------------------------------------
  * Learned Voigt-profile surrogate.  The paper evaluates the Voigt profile of
  * the Core-and-Voigt treatment on the fly (Section 3.2); this library adds a

@@ -591,6 +591,12 @@ def measure_ex2_rate(ctx: Context) -> float:
     return float(v.value)
 
 
+def selftest_wait_timeout(ctx: Context, polls: int = 1000):
+    """Run the bounded-wait self-test (``dex_selftest_wait_timeout``); the next
+    :meth:`Context.check` raises with DEX_ERR_TIMEOUT."""
+    ctx._rc(lib().dex_selftest_wait_timeout(ctx.handle, int(polls)))
+
+
 # ------------------------------------------------------ profile surrogate --
 
 def mlp_param_count() -> int:

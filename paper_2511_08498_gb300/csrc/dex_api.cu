@@ -975,3 +975,13 @@ int dex_measure_ex2_rate(dex_ctx* ctx, double* ops_per_s)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ex2 rate probe");
     return ok(ctx);
 }
+
+int dex_selftest_wait_timeout(dex_ctx* ctx, int polls)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (polls < 1 || polls > 1000000) return fail(ctx, DEX_ERR_ARG, "polls must be in [1, 1e6]");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_wait_timeout(ctx->stream, polls, ctx->status);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "wait self-test launch");
+    return ok(ctx);
+}

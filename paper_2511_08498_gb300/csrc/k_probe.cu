@@ -3,6 +3,7 @@
 // kernels are measured against.  Each thread runs 8 independent chains
 // x <- 2^x * c (c = -1/2 keeps x in (-1, 0]); the grid fills every SM 8 times.
 #include "dex_common.cuh"
+#include "umma.cuh"
 
 namespace dex {
 
@@ -26,7 +27,24 @@ __global__ void __launch_bounds__(256) k_ex2_rate(float* out, int iters)
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// An mbarrier that nothing arrives on: the bounded wait every tensor-core
+// kernel uses must give up after `polls` polls and report DEX_ERR_TIMEOUT,
+// leaving the context usable.
+__global__ void k_wait_timeout(int polls, unsigned int* status)
+{
+    __shared__ unsigned long long mbar;
+    if (threadIdx.x == 0) umma::mbar_init(&mbar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !umma::mbar_wait(&mbar, 0u, polls)) raise_status(status, DEX_ERR_TIMEOUT);
+}
+
 }  // namespace
+
+cudaError_t launch_wait_timeout(cudaStream_t s, int polls, unsigned int* status)
+{
+    k_wait_timeout<<<1, 32, 0, s>>>(polls, status);
+    return cudaGetLastError();
+}
 
 cudaError_t measure_ex2_rate(cudaStream_t s, double* ops_per_s)
 {

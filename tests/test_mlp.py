@@ -187,3 +187,21 @@ def test_surrogate_gain_report(ctx):
     # network's hidden activations alone cost more CUDA-core work per sample
     # than the whole HUM1WEI24 evaluation
     assert np.median(e_voigt) < np.median(e_mlp)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(ctx):
+    """The failure path of every tensor-core kernel's mbarrier wait, made to run
+    out on purpose (a barrier nothing arrives on): the status comes back as
+    DEX_ERR_TIMEOUT at the next check, and the same context then runs a solve."""
+    from paper_2511_08498_gb300 import api
+    from paper_2511_08498_gb300._native import DexError
+    api.selftest_wait_timeout(ctx, 1000)
+    with pytest.raises(DexError) as err:
+        ctx.check()
+    assert err.value.code & 32  # DEX_ERR_TIMEOUT
+    ctx.check()  # the status word was cleared
+    p = synth.mlp.random_params(synth.SEED_BASE + 990, scale=0.3)
+    xau = synth.mlp.voigt_samples(300, seed=synth.SEED_BASE + 991)
+    y = api.mlp_forward(ctx, dev(xau), dev(p)).cpu().numpy()
+    ctx.check()
+    assert np.abs(y - omlp.forward(p, xau, emulate=True)).max() < 2e-3
