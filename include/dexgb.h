@@ -513,8 +513,9 @@ int dex_selftest_wait_timeout(dex_ctx* ctx, int polls);
  *   b2 [64] at 4352, w3 [64] at 4416, b3 at 4480.
  * The kernels use W1, W2, w3 rounded to bfloat16 (round to nearest even) and
  * the bfloat16-rounded h1 as tensor-core operands; all sums are float32.
- * Samples xau are [n][3] float32 (x, a, u), device memory.  A sample with a
- * non-finite value or a <= 0 is skipped and sets DEX_ERR_NUMERIC.
+ * Samples xau are [n][3] float32 (x, a, u), device memory, 0 <= n <= 2^38
+ * (DEX_ERR_ARG otherwise).  A sample with a non-finite value or a <= 0 is
+ * skipped and sets DEX_ERR_NUMERIC.
  * ---------------------------------------------------------------------- */
 int dex_mlp_param_count(void);
 

@@ -904,7 +904,7 @@ int dex_mlp_param_count(void) { return dex::mlp_param_count(); }
 int dex_mlp_forward(dex_ctx* ctx, long long n, const float* xau, const float* params, float* out)
 {
     if (!ctx) return DEX_ERR_ARG;
-    if (n < 0) return fail(ctx, DEX_ERR_ARG, "negative n");
+    if (n < 0 || n > (1LL << 38)) return fail(ctx, DEX_ERR_ARG, "n must be in [0, 2^38]");
     if (n == 0) return ok(ctx);
     if (!xau || !params || !out) return fail(ctx, DEX_ERR_ARG, "null buffer");
     if (int r = bind(ctx)) return r;
@@ -923,7 +923,7 @@ int dex_mlp_grad(dex_ctx* ctx, long long n, const float* xau, const float* targe
                  float* grad, float* loss)
 {
     if (!ctx) return DEX_ERR_ARG;
-    if (n < 0) return fail(ctx, DEX_ERR_ARG, "negative n");
+    if (n < 0 || n > (1LL << 38)) return fail(ctx, DEX_ERR_ARG, "n must be in [0, 2^38]");
     if (!params || !grad || !loss || (n > 0 && (!xau || !target))) return fail(ctx, DEX_ERR_ARG, "null buffer");
     if (int r = bind(ctx)) return r;
     dex::MlpParams P{};
@@ -956,7 +956,7 @@ int dex_mlp_adam(dex_ctx* ctx, float* params, const float* grad, float* m, float
 int dex_mlp_targets(dex_ctx* ctx, long long n, const float* xau, float* out)
 {
     if (!ctx) return DEX_ERR_ARG;
-    if (n < 0) return fail(ctx, DEX_ERR_ARG, "negative n");
+    if (n < 0 || n > (1LL << 38)) return fail(ctx, DEX_ERR_ARG, "n must be in [0, 2^38]");
     if (n == 0) return ok(ctx);
     if (!xau || !out) return fail(ctx, DEX_ERR_ARG, "null buffer");
     if (int r = bind(ctx)) return r;
