@@ -1,9 +1,10 @@
-"""ctypes front end of the float64 long-characteristics oracle (``lc_dense.c``).
+"""ctypes front end of the float64 long-characteristics oracle (``lc_dense.c``;
+the 3D form in ``lc3_dense.c`` is wrapped by ``lc3.py``).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
 benchmark's CPU-baseline leg; never by the product path.
 
-The C file is compiled with the host ``gcc`` into ``oracle/liboracle.so`` on
+The C files are compiled with the host ``gcc`` into ``oracle/liboracle.so`` on
 first use (or by :func:`build`).
 """
 
@@ -17,7 +18,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "lc_dense.c")
+_SRCS = [os.path.join(_HERE, "lc_dense.c"), os.path.join(_HERE, "lc3_dense.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -26,10 +27,10 @@ _lock = threading.Lock()
 def build(force: bool = False) -> str:
     """Compile the oracle's C core (gcc, OpenMP) if missing or stale; return the .so path."""
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(s) for s in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -57,6 +58,16 @@ def lib():
                                                      ctypes.c_int, ip, ctypes.c_double, dp, dp]
             L.oracle_num_threads.restype = ctypes.c_int
             L.oracle_num_threads.argtypes = []
+            ci, cd = ctypes.c_int, ctypes.c_double
+            L.oracle3_ray_segments.restype = ci
+            L.oracle3_ray_segments.argtypes = [ci, ci, ci, cd, cd, cd, cd, cd, cd, ci, ip, dp]
+            L.oracle3_count_segments.restype = ctypes.c_int64
+            L.oracle3_count_segments.argtypes = [ci, ci, ci, ci, dp, ci, ip]
+            L.oracle3_formal_solve.restype = ci
+            L.oracle3_formal_solve.argtypes = [ci, ci, ci, ci, dp, dp, ci, dp, dp, ci, ip, cd, dp, dp]
+            L.oracle3_formal_solve_banded.restype = ci
+            L.oracle3_formal_solve_banded.argtypes = [ci, ci, ci, ci, ci, dp, dp, ip, ci, ci, ci, dp, ci, dp, dp,
+                                                      ci, ip, cd, dp, dp]
             _lib = L
     return _lib
 

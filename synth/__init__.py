@@ -20,3 +20,4 @@ from .atmospheres import (  # noqa: F401
     dynamic_line_atmosphere,
     batch_specs,
 )
+from .atmospheres3 import directions3, sparse_line_atmosphere3, random_medium3  # noqa: F401
