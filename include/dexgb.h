@@ -46,6 +46,7 @@ enum {
 #define DEX_VERSION 100
 #define DEX_MAX_DIRS 256        /* quadrature directions per solve                    */
 #define DEX_BLOCK 16            /* block side of the sparse grid (Section 2.3)        */
+#define DEX_BLOCK3 8            /* block side of the sparse 3D grid (Section 2.3)     */
 #define DEX_STATE_BITS 3        /* bits per packed block state (Section 2.3.1)        */
 #define DEX_STATES_PER_WORD 21  /* floor(64 / 3) block states per 64-bit word         */
 
@@ -540,6 +541,86 @@ int dex_mlp_adam(dex_ctx* ctx, float* params, const float* grad, float* m, float
 /* Training targets ln H(a, x - u) from the library's own Voigt evaluation
  * (dex_voigt's scheme), out[n] device. */
 int dex_mlp_targets(dex_ctx* ctx, long long n, const float* xau, float* out);
+
+/* ============================================================== 3D grids ==
+ *
+ * Section 2.3: the adapted grid "generalises directly to 3D": cubic blocks of
+ * DEX_BLOCK3^3 = 8^3 voxels, each empty or at one MIP level in 0..3 (Section
+ * 2.3.1: a block reduces to a single entry at level 3), MIP groups of 2x2x2
+ * voxels (Section 2.1).  Grids are [nz][ny][nx] with x fastest: cell
+ * c = (k * ny + j) * nx + i.  Directions are host [n_dir][3] (d_x, d_y, d_z)
+ * finite unit vectors, 1 <= n_dir <= DEX_MAX_DIRS, weights host [n_dir].
+ * Every 3D call needs nx * ny * nz <= 2^31 - 1 cells and each extent <= 2048
+ * (the Morton layout walks a cube of at most 256^3 block codes).
+ */
+
+/*
+ * Plain full-resolution 3D formal solution: dex_formal_solve_dense on three
+ * axes.  From the centre of every probe cell along each d_k the ray is traced
+ * to the grid boundary (where the intensity is i_bc) through every voxel with
+ * exact path lengths; I_k and J = sum_k w_k I_k as in 2D.
+ *   planes     device wavelength-batch records of every cell (dex_pack_planes
+ *              with n_cells = nx * ny * nz)
+ *   n_probe    < 0: every cell (probes NULL, probe p = cell p); 0: no-op
+ *   probes     device [n_probe] cell indices
+ *   J          device [n_lambda][n_probe] output (overwritten)
+ *   I          device [n_lambda][n_dir][n_probe] output or NULL
+ *   seg_count  device uint64 accumulator or NULL (non-zero-length segments)
+ */
+int dex_formal_solve_dense3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, const float* planes,
+                            int n_dir, const float* dirs, const float* weights, int n_probe, const int* probes,
+                            float i_bc, float* J, float* I, unsigned long long* seg_count);
+
+/*
+ * Sparsity map and Morton layout of a 3D grid (nx, ny, nz positive multiples of
+ * 8).  A block is empty when eta = chi = 0 in all its cells at every
+ * wavelength; active blocks are ranked along the Z-order curve of (bx, by, bz)
+ * (bit b of bx, by, bz at bits 3b, 3b + 1, 3b + 2).
+ *   eta, chi      device [n_lambda][nz][ny][nx]
+ *   block_offset  device [nbz * nby * nbx] output: rank of block (bz * nby + by) * nbx + bx, or -1
+ *   active        device [nbz * nby * nbx] output: block index of each rank
+ *   n_active      device int output
+ */
+int dex_grid3_build(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, const float* eta, const float* chi,
+                    int* block_offset, int* active, int* n_active);
+
+/* Packed 3-bit block-state words per wavelength batch: ceil(nbx * nby * nbz / 21). */
+size_t dex_state_words3(int nx, int ny, int nz);
+
+/* Voxel records of one 3D chain, levels 0..max_mip (max_mip <= 3): sum (8 >> m)^3. */
+int dex_chain_voxels3(int max_mip);
+
+/* Floats of the 3D brick array: n_batch * capacity * dex_chain_voxels3(max_mip) * record floats. */
+size_t dex_brick3_floats(int capacity, int n_lambda, int W, int max_mip, int storage);
+
+/*
+ * 3D MIP chains and level selection (dex_mips_build on 2x2x2 groups; the IoD
+ * test, always-average rule, means and per-batch level rule are the same).
+ * params->max_mip must be in 0..3.  Level m of a block starts at record
+ * sum_{k<m} (8 >> k)^3 and is row-major [z][y][x] over (8 >> m)^3 voxels.
+ *   level_cap  device [nbz * nby * nbx] per-block upper bound, or NULL
+ *   bricks, state_words  outputs as in dex_mips_build (state words zeroed by the call)
+ */
+int dex_mips3_build(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, const float* eta,
+                    const float* chi, const int* active, const int* n_active, int capacity,
+                    const dex_vlm_params* params, const signed char* level_cap, float* bricks,
+                    unsigned long long* state_words);
+
+/*
+ * Accelerated 3D formal solution (Section 2.3, Algorithm 1 on three axes): from
+ * the centre of every cell of every active block, hierarchical DDA over the
+ * 8^3 blocks, empty blocks crossed in one step, each non-empty block sampled at
+ * its level capped by the distance limits (n_band <= 4 non-decreasing
+ * thresholds, band = NULL for none; as dex_formal_solve_hdda).
+ *   J   device [n_lambda][nz][ny][nx] output; zeroed by the call, written at probe cells
+ *   I   device [n_lambda][n_dir][nz][ny][nx] output or NULL (zeroed by the call)
+ *   seg_count  device uint64 accumulator or NULL: adds the voxel segments integrated
+ */
+int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, int max_mip, int storage,
+                           const float* bricks, const unsigned long long* state_words, const int* block_offset,
+                           const int* active, const int* n_active, int capacity, int n_dir, const float* dirs,
+                           const float* weights, int n_band, const float* band, float i_bc, float* J, float* I,
+                           unsigned long long* seg_count);
 
 #ifdef __cplusplus
 }

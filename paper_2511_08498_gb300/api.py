@@ -670,3 +670,124 @@ def mlp_train(ctx: Context, xau: torch.Tensor, target: torch.Tensor, params: tor
         if log_every and (k % log_every == 0 or k == steps - 1):
             logged.append(float(loss.item()))
     return logged
+
+
+# ------------------------------------------------------------------- 3D --
+
+BLOCK3 = 8
+
+
+def _quadrature3(dirs, weights):
+    d = _host_f32(dirs, (-1, 3))
+    w = _host_f32(weights)
+    if d.shape[0] != w.size:
+        raise ValueError("dirs and weights differ in length")
+    return d, w
+
+
+def formal_solve_dense3(ctx: Context, nx: int, ny: int, nz: int, n_lambda: int, W: int, planes: torch.Tensor,
+                        dirs, weights, probes: torch.Tensor | None = None, i_bc: float = 0.0,
+                        want_intensity: bool = False, count_segments: bool = False,
+                        J: torch.Tensor | None = None):
+    """Plain full-resolution 3D solve (``dex_formal_solve_dense3``); ``planes`` from
+    :func:`pack_planes` over the ``nx * ny * nz`` cells.  Returns ``(J, I, seg)`` as
+    :func:`formal_solve_dense`."""
+    d, w = _quadrature3(dirs, weights)
+    dev = planes.device
+    n_probe = nx * ny * nz if probes is None else int(probes.numel())
+    n_probe_arg = -1 if probes is None else n_probe
+    if J is None:
+        J = torch.empty((n_lambda, n_probe), dtype=torch.float32, device=dev)
+    I = torch.empty((n_lambda, d.shape[0], n_probe), dtype=torch.float32, device=dev) if want_intensity else None
+    seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
+    fp = ctypes.POINTER(ctypes.c_float)
+    ctx._rc(lib().dex_formal_solve_dense3(
+        ctx.handle, nx, ny, nz, n_lambda, W, _ptr(planes), d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp),
+        n_probe_arg, _ptr(probes) if n_probe_arg > 0 else None, float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+    return J, I, seg
+
+
+class SparseGrid3:
+    """Block sparsity map and Morton layout (device tensors) of an nx x ny x nz grid."""
+
+    def __init__(self, nx, ny, nz, block_offset, active, n_active):
+        self.nx, self.ny, self.nz = nx, ny, nz
+        self.nbx, self.nby, self.nbz = nx // BLOCK3, ny // BLOCK3, nz // BLOCK3
+        self.block_offset = block_offset
+        self.active = active
+        self.n_active_dev = n_active
+
+    @property
+    def n_blocks(self):
+        return self.nbx * self.nby * self.nbz
+
+    @property
+    def n_cells(self):
+        return self.nx * self.ny * self.nz
+
+    def n_active(self) -> int:
+        return int(self.n_active_dev.item())
+
+
+def grid3_build(ctx: Context, nx: int, ny: int, nz: int, eta: torch.Tensor, chi: torch.Tensor,
+                out: SparseGrid3 | None = None):
+    """3D sparsity map + Morton-ordered active blocks (``dex_grid3_build``)."""
+    n_lambda = eta.shape[0]
+    nb = (nx // BLOCK3) * (ny // BLOCK3) * (nz // BLOCK3)
+    if out is None:
+        dev = eta.device
+        out = SparseGrid3(nx, ny, nz, torch.empty(nb, dtype=torch.int32, device=dev),
+                          torch.zeros(nb, dtype=torch.int32, device=dev), torch.zeros(1, dtype=torch.int32, device=dev))
+    ctx._rc(lib().dex_grid3_build(ctx.handle, nx, ny, nz, n_lambda, _ptr(eta), _ptr(chi), _ptr(out.block_offset),
+                                  _ptr(out.active), _ptr(out.n_active_dev)))
+    return out
+
+
+def state_words3(nx: int, ny: int, nz: int) -> int:
+    return int(lib().dex_state_words3(nx, ny, nz))
+
+
+def chain_voxels3(max_mip: int) -> int:
+    return int(lib().dex_chain_voxels3(max_mip))
+
+
+def mips3_build(ctx: Context, grid: SparseGrid3, eta, chi, W: int, max_mip: int, iod_eta: float, iod_chi: float,
+                chi_ds_min: float = 0.25, log_mean: bool = False, level_cap: torch.Tensor | None = None,
+                capacity: int | None = None, out: Mips | None = None, storage: int = STORE_F32):
+    """3D MIP chains + VLM block levels of every wavelength batch (``dex_mips3_build``)."""
+    n_lambda = eta.shape[0]
+    cap = grid.n_blocks if capacity is None else int(capacity)
+    n_batch = -(-n_lambda // W)
+    if out is None:
+        nf = int(lib().dex_brick3_floats(cap, n_lambda, W, max_mip, storage))
+        bricks = torch.empty(max(nf, 4), dtype=torch.float32, device=eta.device)
+        words = torch.empty((n_batch, state_words3(grid.nx, grid.ny, grid.nz)), dtype=torch.int64, device=eta.device)
+        out = Mips(bricks, words, W, max_mip, n_lambda, cap, storage)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 1 if log_mean else 0,
+                  int(out.storage))
+    ctx._rc(lib().dex_mips3_build(ctx.handle, grid.nx, grid.ny, grid.nz, n_lambda, W, _ptr(eta), _ptr(chi),
+                                  _ptr(grid.active), _ptr(grid.n_active_dev), cap, ctypes.byref(p), _ptr(level_cap),
+                                  _ptr(out.bricks), _ptr(out.words)))
+    return out
+
+
+def formal_solve_hdda3(ctx: Context, grid: SparseGrid3, mips: Mips, dirs, weights, i_bc: float = 0.0,
+                       want_intensity: bool = False, count_segments: bool = False, J: torch.Tensor | None = None,
+                       band=None):
+    """Accelerated 3D solve (``dex_formal_solve_hdda3``): dense ``J[n_lambda][nz*ny*nx]``
+    (zero outside active blocks), optional I, optional integrated-segment count."""
+    d, w = _quadrature3(dirs, weights)
+    dev = mips.bricks.device
+    n_cells = grid.n_cells
+    if J is None:
+        J = torch.empty((mips.n_lambda, n_cells), dtype=torch.float32, device=dev)
+    I = torch.empty((mips.n_lambda, d.shape[0], n_cells), dtype=torch.float32, device=dev) if want_intensity else None
+    seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
+    fp = ctypes.POINTER(ctypes.c_float)
+    b = None if band is None else _host_f32(band).reshape(-1)
+    ctx._rc(lib().dex_formal_solve_hdda3(
+        ctx.handle, grid.nx, grid.ny, grid.nz, mips.n_lambda, mips.W, mips.max_mip, int(mips.storage),
+        _ptr(mips.bricks), _ptr(mips.words), _ptr(grid.block_offset), _ptr(grid.active), _ptr(grid.n_active_dev),
+        mips.capacity, d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
+        None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
+    return J, I, seg

@@ -985,3 +985,227 @@ int dex_selftest_wait_timeout(dex_ctx* ctx, int polls)
     if (e != cudaSuccess) return cuda_fail(ctx, e, "wait self-test launch");
     return ok(ctx);
 }
+
+// ------------------------------------------------------------------- 3D --
+static int check_extent3(dex_ctx* ctx, int nx, int ny, int nz, bool blocks)
+{
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 2048 || ny > 2048 || nz > 2048)
+        return fail(ctx, DEX_ERR_ARG, "3D grid extents must be in [1, 2048], got %d x %d x %d", nx, ny, nz);
+    if ((long long)nx * ny * nz > 0x7fffffffLL) return fail(ctx, DEX_ERR_ARG, "3D grid above 2^31 - 1 cells");
+    if (blocks && (nx % DEX_BLOCK3 || ny % DEX_BLOCK3 || nz % DEX_BLOCK3))
+        return fail(ctx, DEX_ERR_ARG, "sparse 3D grids need extents that are multiples of %d", DEX_BLOCK3);
+    return DEX_OK;
+}
+
+static int fill_quadrature3(dex_ctx* ctx, int n_dir, const float* dirs, const float* weights, dex::Quadrature3& q)
+{
+    if (n_dir < 1 || n_dir > DEX_MAX_DIRS)
+        return fail(ctx, DEX_ERR_ARG, "n_dir must be in [1, %d], got %d", DEX_MAX_DIRS, n_dir);
+    if (!dirs || !weights) return fail(ctx, DEX_ERR_ARG, "dirs and weights (host arrays) are required");
+    q.n_dir = n_dir;
+    for (int k = 0; k < n_dir; ++k) {
+        const float dx = dirs[3 * k], dy = dirs[3 * k + 1], dz = dirs[3 * k + 2];
+        const float n2 = dx * dx + dy * dy + dz * dz;
+        if (!std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dz) || std::fabs(n2 - 1.0f) > 1e-4f)
+            return fail(ctx, DEX_ERR_ARG, "direction %d is not a finite unit vector", k);
+        if (!std::isfinite(weights[k])) return fail(ctx, DEX_ERR_ARG, "weight %d is not finite", k);
+        q.dx[k] = dx;
+        q.dy[k] = dy;
+        q.dz[k] = dz;
+        q.w[k] = weights[k];
+    }
+    return DEX_OK;
+}
+
+int dex_formal_solve_dense3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, const float* planes,
+                            int n_dir, const float* dirs, const float* weights, int n_probe, const int* probes,
+                            float i_bc, float* J, float* I, unsigned long long* seg_count)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_extent3(ctx, nx, ny, nz, false)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (n_lambda < 0) return fail(ctx, DEX_ERR_ARG, "negative n_lambda");
+    const long long n_cells = (long long)nx * ny * nz;
+    if (n_probe < 0) {
+        if (probes) return fail(ctx, DEX_ERR_ARG, "n_probe < 0 (every cell) takes no probe list");
+        n_probe = (int)n_cells;
+    } else if (n_probe > 0 && !probes) {
+        return fail(ctx, DEX_ERR_ARG, "probe list required for n_probe > 0");
+    }
+    if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
+    dex::Dense3Params P{};
+    if (int r = fill_quadrature3(ctx, n_dir, dirs, weights, P.quad)) return r;
+    if (n_lambda == 0 || n_probe == 0) return ok(ctx);
+    if (!planes || !J) return fail(ctx, DEX_ERR_ARG, "planes and J are required");
+    if (!aligned(planes, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "planes misaligned");
+    P.nx = nx;
+    P.ny = ny;
+    P.nz = nz;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.n_cells = n_cells;
+    P.planes = planes;
+    P.n_probe = n_probe;
+    P.probes = probes;
+    P.i_bc = i_bc;
+    P.J = J;
+    P.I = I;
+    P.seg_count = seg_count;
+    P.status = ctx->status;
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_solve_dense3(ctx->stream, P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_dense3 launch");
+    return ok(ctx);
+}
+
+size_t dex_state_words3(int nx, int ny, int nz)
+{
+    if (nx < DEX_BLOCK3 || ny < DEX_BLOCK3 || nz < DEX_BLOCK3) return 0;
+    const size_t nb = (size_t)(nx / DEX_BLOCK3) * (size_t)(ny / DEX_BLOCK3) * (size_t)(nz / DEX_BLOCK3);
+    return (nb + DEX_STATES_PER_WORD - 1) / DEX_STATES_PER_WORD;
+}
+
+int dex_chain_voxels3(int max_mip)
+{
+    if (max_mip < 0 || max_mip > 3) return 0;
+    return dex::chain_length3(max_mip);
+}
+
+size_t dex_brick3_floats(int capacity, int n_lambda, int W, int max_mip, int storage)
+{
+    if (capacity < 0 || n_lambda < 0 || !valid_W(W) || max_mip < 0 || max_mip > 3 || !valid_storage(W, storage))
+        return 0;
+    const size_t n_batch = (size_t)((n_lambda + W - 1) / W);
+    return n_batch * (size_t)capacity * (size_t)dex::chain_length3(max_mip) * (size_t)dex::record_floats(W, storage);
+}
+
+int dex_grid3_build(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, const float* eta, const float* chi,
+                    int* block_offset, int* active, int* n_active)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_extent3(ctx, nx, ny, nz, true)) return r;
+    if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
+    if (!eta || !chi || !block_offset || !active || !n_active) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_grid3_build(ctx->stream, nx, ny, nz, n_lambda, eta, chi, block_offset, active,
+                                            n_active);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "grid3_build launch");
+    return ok(ctx);
+}
+
+int dex_mips3_build(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, const float* eta, const float* chi,
+                    const int* active, const int* n_active, int capacity, const dex_vlm_params* params,
+                    const signed char* level_cap, float* bricks, unsigned long long* state_words)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_extent3(ctx, nx, ny, nz, true)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
+    if (!params) return fail(ctx, DEX_ERR_ARG, "params required");
+    if (params->max_mip < 0 || params->max_mip > 3)
+        return fail(ctx, DEX_ERR_ARG, "3D max_mip must be in [0, 3], got %d", params->max_mip);
+    if (std::isnan(params->iod_eta) || std::isnan(params->iod_chi) || std::isnan(params->chi_ds_min))
+        return fail(ctx, DEX_ERR_ARG, "NaN threshold");
+    if (!valid_storage(W, params->storage))
+        return fail(ctx, DEX_ERR_ARG, "storage %d not available for W = %d", params->storage, W);
+    const long long nb = (long long)(nx / DEX_BLOCK3) * (ny / DEX_BLOCK3) * (nz / DEX_BLOCK3);
+    if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %lld]", nb);
+    if (!eta || !chi || !active || !n_active || !bricks || !state_words) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    dex::Mip3Params P{};
+    P.nx = nx;
+    P.ny = ny;
+    P.nz = nz;
+    P.nbx = nx / DEX_BLOCK3;
+    P.nby = ny / DEX_BLOCK3;
+    P.nbz = nz / DEX_BLOCK3;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.max_mip = params->max_mip;
+    P.chain = dex::chain_length3(params->max_mip);
+    P.n_words = (int)dex_state_words3(nx, ny, nz);
+    P.cap_active = capacity;
+    P.storage = params->storage;
+    P.log_mean = params->log_mean != 0;
+    P.thr_eta = params->iod_eta;
+    P.thr_chi = params->iod_chi;
+    P.chi_ds_min = params->chi_ds_min;
+    P.eta = eta;
+    P.chi = chi;
+    P.active = active;
+    P.n_active = n_active;
+    P.level_cap = level_cap;
+    P.bricks = bricks;
+    P.words = state_words;
+    P.status = ctx->status;
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_mips3_build(ctx->stream, P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "mips3_build launch");
+    return ok(ctx);
+}
+
+int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, int max_mip, int storage,
+                           const float* bricks, const unsigned long long* state_words, const int* block_offset,
+                           const int* active, const int* n_active, int capacity, int n_dir, const float* dirs,
+                           const float* weights, int n_band, const float* band, float i_bc, float* J, float* I,
+                           unsigned long long* seg_count)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_extent3(ctx, nx, ny, nz, true)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
+    if (max_mip < 0 || max_mip > 3) return fail(ctx, DEX_ERR_ARG, "3D max_mip must be in [0, 3]");
+    if (!valid_storage(W, storage)) return fail(ctx, DEX_ERR_ARG, "storage %d not available for W = %d", storage, W);
+    const long long nb = (long long)(nx / DEX_BLOCK3) * (ny / DEX_BLOCK3) * (nz / DEX_BLOCK3);
+    if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %lld]", nb);
+    if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
+    dex::Hdda3Params P{};
+    P.storage = storage;
+    P.n_band = -1;
+    if (band != nullptr && n_band >= 0) {
+        if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);
+        for (int q = 0; q < n_band; ++q) {
+            if (std::isnan(band[q]) || (q > 0 && band[q] < band[q - 1]))
+                return fail(ctx, DEX_ERR_ARG, "distance thresholds must be non-decreasing numbers");
+            P.band[q] = band[q];
+        }
+        P.n_band = n_band;
+    }
+    if (int r = fill_quadrature3(ctx, n_dir, dirs, weights, P.quad)) return r;
+    if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
+        return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    P.nx = nx;
+    P.ny = ny;
+    P.nz = nz;
+    P.nbx = nx / DEX_BLOCK3;
+    P.nby = ny / DEX_BLOCK3;
+    P.nbz = nz / DEX_BLOCK3;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.max_mip = max_mip;
+    P.chain = dex::chain_length3(max_mip);
+    P.n_words = (int)dex_state_words3(nx, ny, nz);
+    P.cap_active = capacity;
+    P.n_cells = (long long)nx * ny * nz;
+    P.bricks = bricks;
+    P.words = state_words;
+    P.block_offset = block_offset;
+    P.active = active;
+    P.n_active = n_active;
+    P.i_bc = i_bc;
+    P.J = J;
+    P.I = I;
+    P.seg_count = seg_count;
+    P.status = ctx->status;
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
+    if (e == cudaSuccess && I)
+        e = cudaMemsetAsync(I, 0, sizeof(float) * (size_t)n_lambda * (size_t)n_dir * (size_t)P.n_cells, ctx->stream);
+    if (e == cudaSuccess) e = dex::launch_solve_hdda3(ctx->stream, P);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_hdda3 launch");
+    return ok(ctx);
+}

@@ -188,6 +188,71 @@ cudaError_t launch_grid_build(cudaStream_t s, int nx, int nz, int n_lambda, cons
 cudaError_t launch_mips_build(cudaStream_t s, const MipParams& p);
 cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& p);
 
+// ------------------------------------------------------------------- 3D --
+// Grids [nz][ny][nx] (x fastest) cut into DEX_BLOCK3^3 blocks; block index
+// (bz * nby + by) * nbx + bx; level m of a block's chain holds (8 >> m)^3
+// voxels, row-major [z][y][x].
+struct Quadrature3 {
+    int n_dir;
+    float dx[DEX_MAX_DIRS];
+    float dy[DEX_MAX_DIRS];
+    float dz[DEX_MAX_DIRS];
+    float w[DEX_MAX_DIRS];
+};
+
+struct Dense3Params {
+    int nx, ny, nz, n_lambda, W, n_batch;
+    long long n_cells;
+    const float* planes;
+    int n_probe;
+    const int* probes;      // nullptr: every cell
+    float i_bc;
+    float* J;
+    float* I;
+    unsigned long long* seg_count;
+    unsigned int* status;
+    Quadrature3 quad;
+};
+
+struct Mip3Params {
+    int nx, ny, nz, nbx, nby, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active, storage;
+    bool log_mean;
+    float thr_eta, thr_chi, chi_ds_min;
+    const float* eta;
+    const float* chi;
+    const int* active;
+    const int* n_active;
+    const signed char* level_cap;
+    float* bricks;
+    unsigned long long* words;
+    unsigned int* status;
+};
+
+struct Hdda3Params {
+    int nx, ny, nz, nbx, nby, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active, storage;
+    int n_band;
+    float band[4];
+    long long n_cells;
+    const float* bricks;
+    const unsigned long long* words;
+    const int* block_offset;
+    const int* active;
+    const int* n_active;
+    float i_bc;
+    float* J;
+    float* I;
+    unsigned long long* seg_count;
+    unsigned int* status;
+    Quadrature3 quad;
+};
+
+int chain_length3(int max_mip);
+cudaError_t launch_solve_dense3(cudaStream_t s, const Dense3Params& P);
+cudaError_t launch_grid3_build(cudaStream_t s, int nx, int ny, int nz, int n_lambda, const float* eta, const float* chi,
+                               int* block_offset, int* active, int* n_active);
+cudaError_t launch_mips3_build(cudaStream_t s, const Mip3Params& P);
+cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P);
+
 cudaError_t launch_pack_planes(cudaStream_t s, long long n_cells, int n_lambda, int W,
                                const float* eta, const float* chi, float* planes, unsigned int* status);
 cudaError_t launch_solve_dense(cudaStream_t s, const DenseParams& p);

@@ -31,3 +31,31 @@ def robust_level_mask(stats, level_map, lambda_batch, block, max_mip, te, tc, cm
                     good = good and rf[L_][b, bz, bx]
                 ok[b, bz, bx] = good
     return ok
+
+
+def robust_level_mask3(stats, level_map, lambda_batch, max_mip, te, tc, cm, eps=1e-4):
+    """3D form of :func:`robust_level_mask`: level_map ``[n_batch][nbz][nby][nbx]``."""
+    n_batch, nbz, nby, nbx = level_map.shape
+    rp, rf = [], []
+    for st in stats:
+        L = st["iod_eta"].shape[0]
+        with np.errstate(invalid="ignore"):
+            p = ((st["iod_eta"] < te * (1 - eps)) & (st["iod_chi"] < tc * (1 - eps))) | (st["chi_ds"] < cm * (1 - eps))
+            f = ((st["iod_eta"] > te * (1 + eps)) | (st["iod_chi"] > tc * (1 + eps))) & (st["chi_ds"] > cm * (1 + eps))
+        s = p.shape[1] // nbz
+
+        def per_batch(a, red):
+            blk = red(a.reshape(L, nbz, s, nby, s, nbx, s), axis=(2, 4, 6))
+            return np.stack([red(blk[b * lambda_batch:(b + 1) * lambda_batch], axis=0) for b in range(n_batch)])
+        rp.append(per_batch(p, np.all))
+        rf.append(per_batch(f, np.any))
+    ok = np.ones(level_map.shape, dtype=bool)
+    for idx in np.ndindex(*level_map.shape):
+        L_ = level_map[idx]
+        if L_ < 0:
+            continue
+        good = all(rp[m - 1][idx] for m in range(1, L_ + 1))
+        if L_ < max_mip:
+            good = good and rf[L_][idx]
+        ok[idx] = good
+    return ok

@@ -59,3 +59,17 @@ def test_context_creation_fails_cleanly_without_gpu():
     h = ctypes.c_void_p()
     assert _native.lib().dex_ctx_create(0, None, ctypes.byref(h)) == 2  # DEX_ERR_CUDA
     assert not h.value
+
+
+def test_3d_size_arithmetic():
+    # 8^3 blocks with levels 0..3: 512 + 64 + 8 + 1 = 585 records (1.14x MIP 0, Section 2.1);
+    # states: 3 bits, 21 per 64-bit word (Section 2.3.1), so a 512^3 grid's 262144
+    # blocks take ceil(262144 / 21) = 12484 words.
+    L = _native.lib()
+    assert [L.dex_chain_voxels3(m) for m in range(4)] == [512, 576, 584, 585]
+    assert L.dex_chain_voxels3(4) == 0
+    assert L.dex_state_words3(512, 512, 512) == -(-262144 // 21) == 12484
+    assert L.dex_state_words3(8, 8, 8) == 1
+    assert L.dex_brick3_floats(10, 9, 8, 3, 0) == 2 * 10 * 585 * 16
+    assert L.dex_brick3_floats(10, 9, 8, 3, 1) == 2 * 10 * 585 * 8
+    assert L.dex_brick3_floats(10, 9, 8, 4, 0) == 0
