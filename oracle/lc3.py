@@ -79,17 +79,14 @@ def formal_solve_banded(levels, level_map, block: int, lambda_batch: int, band, 
                         i_bc: float = 0.0, want_intensity: bool = False):
     """3D formal solution over MIP levels with a distance-limited level per block visit.
 
-    levels: list of (eta_m, chi_m) ``[L][nz >> m][ny >> m][nx >> m]`` (``mips3.mip_chain``);
-    level_map: ``[n_batch][nbz][nby][nbx]``; band: thresholds d_1 <= d_2 <= ... (level m
-    allowed in blocks first entered at t >= d_m).
+    levels: list of (eta_m, chi_m) ``[L][nz >> m][ny >> m][nx >> m]`` (``mips3.mip_chain``),
+    passed at their own resolution; level_map: ``[n_batch][nbz][nby][nbx]``; band:
+    thresholds d_1 <= d_2 <= ... (level m allowed in blocks first entered at t >= d_m).
     """
     L, nz, ny, nx = levels[0][0].shape
     n_lev = len(levels)
-    le = np.empty((n_lev, L, nz, ny, nx))
-    lch = np.empty((n_lev, L, nz, ny, nx))
-    for m, (em, cm) in enumerate(levels):
-        le[m] = upsample(em, 2 ** m)
-        lch[m] = upsample(cm, 2 ** m)
+    le = np.ascontiguousarray(np.concatenate([np.asarray(e, np.float64).reshape(-1) for e, _ in levels]))
+    lch = np.ascontiguousarray(np.concatenate([np.asarray(c, np.float64).reshape(-1) for _, c in levels]))
     lm = np.ascontiguousarray(np.asarray(level_map, dtype=np.int32))
     b = np.ascontiguousarray(np.asarray(band, dtype=np.float64).reshape(-1))
     d = np.ascontiguousarray(np.asarray(dirs, dtype=np.float64).reshape(-1, 3))

@@ -191,8 +191,9 @@ int oracle3_formal_solve(int nx, int ny, int nz, int n_lambda, const double* eta
  * block visit (the long-characteristics form of Section 4.1's per-cascade
  * limit): a block first entered at ray parameter t is sampled at level
  * min(L_block, #{band[m-1] <= t}).
- *   lev_eta, lev_chi : [n_lev][n_lambda][nz][ny][nx], entry = the value of the
- *                      level-m voxel containing the cell
+ *   lev_eta, lev_chi : the levels 0..n_lev-1 one after the other, level m as
+ *                      [n_lambda][nz >> m][ny >> m][nx >> m] (the voxel of level m
+ *                      holding cell (i, j, k) is (i >> m, j >> m, k >> m))
  *   block_level      : [n_batch][nbz][nby][nbx] (-1 = empty block)
  */
 int oracle3_formal_solve_banded(int nx, int ny, int nz, int n_lambda, int n_lev, const double* lev_eta,
@@ -202,9 +203,15 @@ int oracle3_formal_solve_banded(int nx, int ny, int nz, int n_lambda, int n_lev,
                                 double* I)
 {
     int cap = 3 * (nx + ny + nz) + 8;
-    size_t vol = (size_t)nx * ny * nz;
     int nbx = nx / block, nby = ny / block, nbz = nz / block;
     size_t nb = (size_t)nbx * nby * nbz;
+    size_t lev_off[8];
+    size_t off = 0;
+    if (n_lev < 1 || n_lev > 8) return -1;
+    for (int m = 0; m < n_lev; ++m) {
+        lev_off[m] = off;
+        off += (size_t)n_lambda * (size_t)(nz >> m) * (size_t)(ny >> m) * (size_t)(nx >> m);
+    }
     int err = 0;
 #pragma omp parallel
     {
@@ -246,8 +253,11 @@ int oracle3_formal_solve_banded(int nx, int ny, int nz, int n_lambda, int n_lev,
                         if (L < 0) continue;
                         int m = L < mcap[s] ? L : mcap[s];
                         if (m >= n_lev) m = n_lev - 1;
-                        size_t off = ((size_t)m * n_lambda + l) * vol + (size_t)cell[s];
-                        double x = lev_chi[off], e = lev_eta[off];
+                        int c = cell[s];
+                        int ci = (c % nx) >> m, cj = ((c / nx) % ny) >> m, ck = (c / (nx * ny)) >> m;
+                        size_t idx = lev_off[m] +
+                                     (((size_t)l * (nz >> m) + ck) * (size_t)(ny >> m) + cj) * (size_t)(nx >> m) + ci;
+                        double x = lev_chi[idx], e = lev_eta[idx];
                         if (x > 0.0) {
                             double tau = x * len[s];
                             inten = inten * exp(-tau) + (e / x) * (-expm1(-tau));

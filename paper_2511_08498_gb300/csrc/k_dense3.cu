@@ -4,7 +4,9 @@
 //
 // Thread = (probe, wavelength batch), looping over the quadrature so that
 // J = sum_k w_k I_k stays in registers; consecutive threads hold consecutive
-// probes (neighbouring cells along x for the all-cell solve).  Records are the
+// probes (neighbouring cells along x for the all-cell solve).  Registers are
+// bounded for 3 CTAs per SM: the solve waits on record loads that miss L2 once
+// the planes outgrow it, and the extra resident warps hide that latency.  Records are the
 // packed (S, chi) wavelength-batch planes of dex_pack_planes.  Plane parameters
 // use the two-float hi + lo form of AxisParam on every axis, so path lengths
 // are accurate relative to the segment and the exit plane is hit exactly.
@@ -15,7 +17,7 @@ namespace dex {
 namespace {
 
 template <int W, bool COUNT>
-__global__ void __launch_bounds__(256) k_solve_dense3(const Dense3Params P)
+__global__ void __launch_bounds__(256, 3) k_solve_dense3(const Dense3Params P)
 {
     const int b = blockIdx.y;
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -85,9 +87,15 @@ __global__ void __launch_bounds__(256) k_solve_dense3(const Dense3Params P)
             if (!COUNT && (it & 15) == 15 && all_opaque<W>(T)) break;
             th_prev = th;
             tl_prev = tl;
-            if (axis == 0) { Px += (float)sx; ci += sx; rp += stepx; }
-            else if (axis == 1) { Py += (float)sy; cj += sy; rp += stepy; }
-            else { Pz += (float)sz; ck += sz; rp += stepz; }
+            // the step on the chosen axis as selects (lanes may step on different axes)
+            const bool a0 = axis == 0, a1 = axis == 1, a2 = axis == 2;
+            Px = a0 ? Px + (float)sx : Px;
+            Py = a1 ? Py + (float)sy : Py;
+            Pz = a2 ? Pz + (float)sz : Pz;
+            ci += a0 ? sx : 0;
+            cj += a1 ? sy : 0;
+            ck += a2 ? sz : 0;
+            rp += a0 ? stepx : (a1 ? stepy : stepz);
         }
         const float wk = P.quad.w[q];
 #pragma unroll

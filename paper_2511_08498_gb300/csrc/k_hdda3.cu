@@ -92,24 +92,21 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
         const float* cur_rp = rp;
         if (!last) {
             if (it >= cap) { capped = true; break; }
+            // the step on the chosen axis, written as selects (no divergent branch
+            // when the lanes of a warp step on different axes)
             const float fv = (float)vox;
-            bool cross;
-            if (axis == 0) {
-                lx += sx;
-                Px += negx ? -fv : fv;
-                rp += negx ? -REC : REC;
-                cross = (unsigned)lx >= (unsigned)side;
-            } else if (axis == 1) {
-                ly += sy;
-                Py += negy ? -fv : fv;
-                rp += (negy ? -side : side) * REC;
-                cross = (unsigned)ly >= (unsigned)side;
-            } else {
-                lz += sz;
-                Pz += negz ? -fv : fv;
-                rp += (negz ? -side * side : side * side) * REC;
-                cross = (unsigned)lz >= (unsigned)side;
-            }
+            const bool a0 = axis == 0, a1 = axis == 1;
+            lx += a0 ? sx : 0;
+            ly += a1 ? sy : 0;
+            lz += (!a0 && !a1) ? sz : 0;
+            Px = a0 ? (negx ? Px - fv : Px + fv) : Px;
+            Py = a1 ? (negy ? Py - fv : Py + fv) : Py;
+            Pz = (!a0 && !a1) ? (negz ? Pz - fv : Pz + fv) : Pz;
+            const int st_ax = a0 ? 1 : (a1 ? side : side * side);
+            const bool ng = a0 ? negx : (a1 ? negy : negz);
+            rp += (ng ? -st_ax : st_ax) * REC;
+            const int la = a0 ? lx : (a1 ? ly : lz);
+            const bool cross = (unsigned)la >= (unsigned)side;
             // early termination where the ray enters another block, once every
             // transmission is exactly zero (the rest adds exact zeros: bit-identical)
             if (cross && all_opaque<W>(T)) break;
