@@ -18,7 +18,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "lc_dense.c"), os.path.join(_HERE, "lc3_dense.c")]
+_SRCS = [os.path.join(_HERE, "lc_dense.c"), os.path.join(_HERE, "lc3_dense.c"), os.path.join(_HERE, "rc_dense.c")]
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 _lock = threading.Lock()
@@ -65,6 +65,9 @@ def lib():
             L.oracle3_count_segments.argtypes = [ci, ci, ci, ci, dp, ci, ip]
             L.oracle3_formal_solve.restype = ci
             L.oracle3_formal_solve.argtypes = [ci, ci, ci, ci, dp, dp, ci, dp, dp, ci, ip, cd, dp, dp]
+            L.oracle_rc_intervals.restype = ci
+            L.oracle_rc_intervals.argtypes = [ci, ci, ci, dp, dp, ci, ci, dp, cd, cd, dp, dp,
+                                              ctypes.POINTER(ctypes.c_ubyte)]
             L.oracle3_formal_solve_banded.restype = ci
             L.oracle3_formal_solve_banded.argtypes = [ci, ci, ci, ci, ci, dp, dp, ip, ci, ci, ci, dp, ci, dp, dp,
                                                       ci, ip, cd, dp, dp]

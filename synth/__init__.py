@@ -19,5 +19,6 @@ from .atmospheres import (  # noqa: F401
     random_medium,
     dynamic_line_atmosphere,
     batch_specs,
+    rc_directions,
 )
 from .atmospheres3 import directions3, sparse_line_atmosphere3, random_medium3  # noqa: F401

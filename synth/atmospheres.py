@@ -279,3 +279,12 @@ def batch_specs(n_atm: int = 24, seed: int = SEED_BASE + 5, sizes=((256, 256), (
                     "n_dir": int(rng.integers(n_dir[0] // 8, n_dir[1] // 8 + 1)) * 8,
                     "empty_frac": float(rng.uniform(*empty)), "seed": int(seed * 100 + a)})
     return out
+
+
+def rc_directions(n0: int = 4, n_cascades: int = 6):
+    """Direction sets of radiance cascades with branching factor 2: cascade i has
+    n0 * 4^i in-plane directions theta_k = 2*pi*(k + 1/2) / (n0 * 4^i), so that
+    directions 4k .. 4k+3 of cascade i + 1 split direction k of cascade i.
+    Returns a list of float32 ``[n_i][2]`` arrays (x, z components); cascade 0
+    equals ``directions(n0)``."""
+    return [directions(n0 * 4 ** i)[0] for i in range(n_cascades)]
