@@ -622,6 +622,45 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
                            const float* weights, int n_band, const float* band, float i_bc, float* J, float* I,
                            unsigned long long* seg_count);
 
+/* ===================================================== radiance cascades ==
+ *
+ * The radiance-cascade formal solution the paper's code wraps around its
+ * traversal (Section 4.1 "Model Configuration"), in 2D: with branching factor 2
+ * cascade i has probes on a lattice of spacing 2^i (probe (px, pz) at
+ * (2^i (px + 1/2), 2^i (pz + 1/2))), n0 4^i directions and the radiance
+ * interval [t0 4^(i-1), t0 4^i] (cascade 0: [0, t0]; the paper: n0 = 4,
+ * t0 = 1.5, 6 cascades, level caps [0, 0, 1, 2, 3, 4]).  Each interval is
+ * traced through the sparse mipmapped grid of dex_mips_build at
+ * min(block level, level_cap[i]) (empty blocks skipped), giving emission I and
+ * transmission T.  Merged radiance L = I + T R, from the top cascade down: R is
+ * i_bc if the ray leaves the grid inside its interval or on the top cascade,
+ * else the bilinear interpolation at the probe of the mean over the 4 child
+ * directions 4k .. 4k+3 of the cascade above (4 nearest probes, indices clamped
+ * at the lattice edge).  J = the mean of L over the n0 cascade-0 directions.
+ */
+
+/* Floats of the workspace: 2 * n_batch * n0 * nx * nz * W (two cascades' merged radiance). */
+size_t dex_rc_workspace_floats(int nx, int nz, int n_lambda, int W, int n0);
+
+/*
+ *   nx, nz        multiples of 16 and of 2^(n_cascades - 1); n0 * nx * nz <= 2^31 - 1
+ *   bricks ... capacity, max_mip, storage: from dex_grid_build / dex_mips_build
+ *                 (storage: F32 with W = 1, 2, 4, 8; BF16 or F16 with W = 8)
+ *   n_cascades    1 .. 8;  n0: 1 .. 64 cascade-0 directions;  t0 > 0 (cascade-0 interval end)
+ *   level_cap     host [n_cascades], each in 0 .. max_mip
+ *   dirs          device [sum_i n0 4^i][2]: the directions of cascade 0, then 1, ...
+ *                 (unit vectors; direction k of cascade i+1's block 4k .. 4k+3 should
+ *                 split direction k of cascade i)
+ *   workspace     device, dex_rc_workspace_floats floats (16-byte aligned)
+ *   J             device [n_lambda][nz][nx] output: zeroed by the call, written at every
+ *                 cell of every non-empty block
+ *   seg_count     device uint64 accumulator or NULL: adds the voxel segments integrated
+ */
+int dex_rc_solve(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, int storage, const float* bricks,
+                 const unsigned long long* state_words, const int* block_offset, int capacity, int n_cascades,
+                 int n0, float t0, const int* level_cap, const float* dirs, float i_bc, float* workspace, float* J,
+                 unsigned long long* seg_count);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,10 @@ PROTOTYPES = {
     "dex_mlp_adam": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float,
                              ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "dex_mlp_targets": (c_int, [c_void_p, ctypes.c_longlong, c_void_p, c_void_p]),
+    "dex_rc_workspace_floats": (c_size_t, [c_int, c_int, c_int, c_int, c_int]),
+    "dex_rc_solve": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p, c_void_p, c_void_p, c_int,
+                             c_int, c_int, c_float, ctypes.POINTER(c_int), c_void_p, c_float, c_void_p, c_void_p,
+                             c_void_p]),
     "dex_formal_solve_dense3": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_void_p, c_int, c_fp, c_fp,
                                         c_int, c_void_p, c_float, c_void_p, c_void_p, c_void_p]),
     "dex_grid3_build": (c_int, [c_void_p, c_int, c_int, c_int, c_int] + [c_void_p] * 5),

@@ -791,3 +791,53 @@ def formal_solve_hdda3(ctx: Context, grid: SparseGrid3, mips: Mips, dirs, weight
         mips.capacity, d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp), -1 if b is None else b.size,
         None if b is None else b.ctypes.data_as(fp), float(i_bc), _ptr(J), _ptr(I), _ptr(seg)))
     return J, I, seg
+
+
+# ------------------------------------------------------ radiance cascades --
+
+RC_LEVEL_CAP = (0, 0, 1, 2, 3, 4)
+
+
+def rc_directions(n0: int, n_cascades: int) -> np.ndarray:
+    """Directions of every cascade, concatenated: cascade i has n0 4^i directions
+    theta_k = 2 pi (k + 1/2) / (n0 4^i) (float32 of the float64 cosine and sine)."""
+    out = []
+    for i in range(n_cascades):
+        n = n0 * 4 ** i
+        th = 2.0 * np.pi * (np.arange(n, dtype=np.float64) + 0.5) / n
+        out.append(np.stack([np.cos(th), np.sin(th)], axis=1).astype(np.float32))
+    return np.concatenate(out)
+
+
+def rc_workspace_floats(nx: int, nz: int, n_lambda: int, W: int, n0: int) -> int:
+    return int(lib().dex_rc_workspace_floats(nx, nz, n_lambda, W, n0))
+
+
+def rc_solve(ctx: Context, grid: SparseGrid, mips: Mips, n_cascades: int = 6, n0: int = 4, t0: float = 1.5,
+             level_cap=None, dirs=None, i_bc: float = 0.0, J: torch.Tensor | None = None,
+             workspace: torch.Tensor | None = None, count_segments: bool = False):
+    """Radiance-cascade formal solution over the sparse mipmapped grid (``dex_rc_solve``).
+
+    ``level_cap``: per-cascade maximum MIP level (default the paper's [0, 0, 1, 2, 3, 4],
+    truncated to ``n_cascades`` and clipped to the chains' top level); ``dirs``: every
+    cascade's directions concatenated (default :func:`rc_directions`).  Returns
+    ``(J, seg)`` with dense ``J[n_lambda][nz*nx]`` (zero outside non-empty blocks)."""
+    dev = mips.bricks.device
+    if level_cap is None:
+        level_cap = [min(c, mips.max_mip) for c in (list(RC_LEVEL_CAP) + [4] * 8)[:n_cascades]]
+    caps = (ctypes.c_int * n_cascades)(*[int(c) for c in level_cap])
+    d = rc_directions(n0, n_cascades) if dirs is None else np.concatenate([np.asarray(x, np.float32).reshape(-1, 2)
+                                                                             for x in dirs])
+    d_dev = torch.from_numpy(np.ascontiguousarray(d)).to(dev)
+    n_cells = grid.nx * grid.nz
+    if J is None:
+        J = torch.empty((mips.n_lambda, n_cells), dtype=torch.float32, device=dev)
+    if workspace is None:
+        nf = rc_workspace_floats(grid.nx, grid.nz, mips.n_lambda, mips.W, n0)
+        workspace = torch.empty(max(nf, 4), dtype=torch.float32, device=dev)
+    seg = torch.zeros(1, dtype=torch.int64, device=dev) if count_segments else None
+    ctx._rc(lib().dex_rc_solve(ctx.handle, grid.nx, grid.nz, mips.n_lambda, mips.W, mips.max_mip, int(mips.storage),
+                               _ptr(mips.bricks), _ptr(mips.words), _ptr(grid.block_offset), mips.capacity,
+                               n_cascades, n0, float(t0), caps, _ptr(d_dev), float(i_bc), _ptr(workspace), _ptr(J),
+                               _ptr(seg)))
+    return J, seg

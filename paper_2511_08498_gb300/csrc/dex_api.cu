@@ -1209,3 +1209,89 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
     if (e != cudaSuccess) return cuda_fail(ctx, e, "solve_hdda3 launch");
     return ok(ctx);
 }
+
+// ----------------------------------------------------- radiance cascades --
+size_t dex_rc_workspace_floats(int nx, int nz, int n_lambda, int W, int n0)
+{
+    if (nx < 1 || nz < 1 || n_lambda < 0 || !valid_W(W) || n0 < 1) return 0;
+    const size_t n_batch = (size_t)((n_lambda + W - 1) / W);
+    return 2 * n_batch * (size_t)n0 * (size_t)nx * (size_t)nz * (size_t)W;
+}
+
+int dex_rc_solve(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, int storage, const float* bricks,
+                 const unsigned long long* state_words, const int* block_offset, int capacity, int n_cascades,
+                 int n0, float t0, const int* level_cap, const float* dirs, float i_bc, float* workspace, float* J,
+                 unsigned long long* seg_count)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (int r = check_sparse_grid(ctx, nx, nz)) return r;
+    if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
+    if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
+    if (max_mip < 0 || max_mip > 4) return fail(ctx, DEX_ERR_ARG, "max_mip must be in [0, 4]");
+    if (!(storage == DEX_STORE_F32 || (W == 8 && (storage == DEX_STORE_BF16 || storage == DEX_STORE_F16))))
+        return fail(ctx, DEX_ERR_ARG, "storage %d not available for W = %d", storage, W);
+    if (n_cascades < 1 || n_cascades > 8) return fail(ctx, DEX_ERR_ARG, "n_cascades must be in [1, 8]");
+    if (n0 < 1 || n0 > 64) return fail(ctx, DEX_ERR_ARG, "n0 must be in [1, 64]");
+    const int top = 1 << (n_cascades - 1);
+    if (nx % top || nz % top)
+        return fail(ctx, DEX_ERR_ARG, "nx, nz must be multiples of 2^(n_cascades - 1) = %d", top);
+    if ((long long)n0 * nx * nz > 0x7fffffffLL) return fail(ctx, DEX_ERR_ARG, "n0 * nx * nz above 2^31 - 1");
+    if (!(t0 > 0.0f) || !std::isfinite(t0)) return fail(ctx, DEX_ERR_ARG, "t0 must be a positive number");
+    if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
+    if (!level_cap) return fail(ctx, DEX_ERR_ARG, "level_cap (host) required");
+    for (int i = 0; i < n_cascades; ++i)
+        if (level_cap[i] < 0 || level_cap[i] > max_mip)
+            return fail(ctx, DEX_ERR_ARG, "level_cap[%d] must be in [0, max_mip]", i);
+    const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
+    if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
+    if (!bricks || !state_words || !block_offset || !dirs || !workspace || !J)
+        return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(bricks, W == 1 ? 8 : 16) || !aligned(workspace, 16)) return fail(ctx, DEX_ERR_ARG, "misaligned buffer");
+    dex::RcParams P{};
+    P.nx = nx;
+    P.nz = nz;
+    P.nbx = nx / DEX_BLOCK;
+    P.nbz = nz / DEX_BLOCK;
+    P.n_lambda = n_lambda;
+    P.W = W;
+    P.n_batch = (n_lambda + W - 1) / W;
+    P.chain = dex::chain_length(max_mip);
+    P.n_words = (int)dex_state_words(nx, nz);
+    P.cap_active = capacity;
+    P.storage = storage;
+    P.i_bc = i_bc;
+    P.bricks = bricks;
+    P.words = state_words;
+    P.block_offset = block_offset;
+    P.seg_count = seg_count;
+    P.status = ctx->status;
+    if (int r = bind(ctx)) return r;
+    const size_t n_cells = (size_t)nx * nz;
+    const size_t half = (size_t)P.n_batch * (size_t)n0 * n_cells * (size_t)W;
+    cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * n_cells, ctx->stream);
+    // direction offsets: cascade i starts at n0 (4^i - 1) / 3
+    const float* upper = nullptr;
+    float* out = nullptr;
+    for (int i = n_cascades - 1; i >= 0 && e == cudaSuccess; --i) {
+        const long long pow4 = 1LL << (2 * i);
+        P.spacing = 1 << i;
+        P.pnx = nx >> i;
+        P.pnz = nz >> i;
+        P.n_dir = (int)(n0 * pow4);
+        P.level_cap = level_cap[i];
+        P.t_s = i == 0 ? 0.0f : t0 * (float)(pow4 / 4);
+        P.t_e = t0 * (float)pow4;
+        P.dirs = dirs + 2 * (size_t)(n0 * ((pow4 - 1) / 3));
+        out = workspace + ((n_cascades - 1 - i) % 2 == 0 ? 0 : half);
+        P.upper = upper;
+        P.out = out;
+        e = dex::launch_rc_cascade(ctx->stream, P);
+        upper = out;
+    }
+    if (e == cudaSuccess) {
+        P.n_dir = n0;
+        e = dex::launch_rc_mean(ctx->stream, P, out, J);
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "rc_solve launch");
+    return ok(ctx);
+}

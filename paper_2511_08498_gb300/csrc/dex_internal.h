@@ -188,6 +188,23 @@ cudaError_t launch_grid_build(cudaStream_t s, int nx, int nz, int n_lambda, cons
 cudaError_t launch_mips_build(cudaStream_t s, const MipParams& p);
 cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& p);
 
+// --------------------------------------------------- radiance cascades --
+struct RcParams {
+    int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
+    int spacing, pnx, pnz, n_dir, level_cap;  // this cascade: probe lattice, directions, MIP cap
+    float t_s, t_e, i_bc;                      // radiance interval, boundary intensity
+    const float* bricks;
+    const unsigned long long* words;
+    const int* block_offset;
+    const float* dirs;                         // [n_dir][2] of this cascade
+    const float* upper;                        // merged radiance of the cascade above, or nullptr
+    float* out;                                // [n_batch][n_dir][pnz * pnx][W] merged radiance
+    unsigned long long* seg_count;
+    unsigned int* status;
+};
+cudaError_t launch_rc_cascade(cudaStream_t s, const RcParams& P);
+cudaError_t launch_rc_mean(cudaStream_t s, const RcParams& P, const float* L0, float* J);
+
 // ------------------------------------------------------------------- 3D --
 // Grids [nz][ny][nx] (x fastest) cut into DEX_BLOCK3^3 blocks; block index
 // (bz * nby + by) * nbx + bx; level m of a block's chain holds (8 >> m)^3
