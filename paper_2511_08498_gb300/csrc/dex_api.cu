@@ -1211,6 +1211,9 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
 }
 
 // ----------------------------------------------------- radiance cascades --
+// cascades with at least this many directions order their threads directions
+// first (measured on the 1024^2 workload: cascades 4 and 5 of the paper's six)
+static constexpr int kRcDirFastestMin = 1024;
 size_t dex_rc_workspace_floats(int nx, int nz, int n_lambda, int W, int n0)
 {
     if (nx < 1 || nz < 1 || n_lambda < 0 || !valid_W(W) || n0 < 1) return 0;
@@ -1279,6 +1282,9 @@ int dex_rc_solve(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip,
         P.pnz = nz >> i;
         P.n_dir = (int)(n0 * pow4);
         P.level_cap = level_cap[i];
+        // long intervals from few probes: a warp of neighbouring directions from one
+        // probe reads neighbouring bricks; short ones keep lanes on neighbouring probes
+        P.dir_fastest = P.n_dir >= kRcDirFastestMin ? 1 : 0;
         P.t_s = i == 0 ? 0.0f : t0 * (float)(pow4 / 4);
         P.t_e = t0 * (float)pow4;
         P.dirs = dirs + 2 * (size_t)(n0 * ((pow4 - 1) / 3));

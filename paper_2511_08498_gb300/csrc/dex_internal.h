@@ -192,6 +192,7 @@ cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& p);
 struct RcParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int spacing, pnx, pnz, n_dir, level_cap;  // this cascade: probe lattice, directions, MIP cap
+    int dir_fastest;                           // thread order: directions (1) or probes (0) fastest
     float t_s, t_e, i_bc;                      // radiance interval, boundary intensity
     const float* bricks;
     const unsigned long long* words;

@@ -9,8 +9,11 @@
 //   on the top cascade), else the bilinear interpolation at this probe of the
 //   mean over the 4 child directions (4k .. 4k+3) of the cascade above (its 4
 //   nearest probes, indices clamped at the lattice edge).
-// Thread = (direction, probe) of one wavelength batch, probes fastest, so the
-// lanes of a warp trace parallel rays from neighbouring probes.  Cascade 0 skips
+// Thread = (direction, probe) of one wavelength batch.  On the lower cascades
+// probes run fastest, so the lanes of a warp trace parallel rays from
+// neighbouring probes; on the upper ones (long intervals from probes 16 or more
+// cells apart) directions run fastest, so a warp's rays fan out from one probe
+// and read neighbouring bricks.  Cascade 0 skips
 // probes in empty blocks (J is not defined there).  A final kernel averages the
 // cascade-0 radiance over its directions into J.
 //
@@ -157,8 +160,14 @@ __global__ void __launch_bounds__(256, 4) k_rc_cascade(const RcParams P)
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n_probe = (long long)P.pnx * P.pnz;
     if (g >= n_probe * P.n_dir) return;
-    const int k = (int)(g / n_probe);
-    const int p = (int)(g - (long long)k * n_probe);
+    int k, p;
+    if (P.dir_fastest) {  // lanes: neighbouring directions of one probe
+        p = (int)(g / P.n_dir);
+        k = (int)(g - (long long)p * P.n_dir);
+    } else {              // lanes: neighbouring probes, one direction
+        k = (int)(g / n_probe);
+        p = (int)(g - (long long)k * n_probe);
+    }
     const int px = p % P.pnx, pz = p / P.pnx;
     const unsigned long long* words = P.words + (size_t)b * P.n_words;
     if (P.spacing == 1) {  // cascade 0: probes only in non-empty blocks
@@ -207,7 +216,7 @@ __global__ void __launch_bounds__(256, 4) k_rc_cascade(const RcParams P)
             for (int w = 0; w < W; ++w) R[w] = fmaf(ws[c] * 0.25f, m[w], R[w]);
         }
     }
-    float* dst = P.out + ((size_t)b * (size_t)P.n_dir * n_probe + (size_t)g) * W;
+    float* dst = P.out + ((size_t)b * (size_t)P.n_dir * n_probe + (size_t)k * n_probe + p) * W;
 #pragma unroll
     for (int w = 0; w < W; ++w) dst[w] = fmaf(T[w], R[w], I[w]);
     if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);

@@ -125,3 +125,15 @@ def test_rc_bf16_bricks_level0(ctx):
     Sb, cb = _bf16(S).astype(np.float64), _bf16(c32).astype(np.float64)
     Jr, probes = oracle_rc(Sb * cb, cb, 8, 0, 1e30, 3, 4, [0, 0, 0])
     assert_rel(J[:, probes], Jr[:, probes], what="J")
+
+
+def test_rc_paper_configuration_512(ctx):
+    # the cascade report's configuration (6 cascades, caps [0, 0, 1, 2, 3, 3], VLM 0-3)
+    # on a 512^2 instance of its workload, every probe of every non-empty block
+    nx = nz = 512
+    L = 8
+    eg, cg, e, c = line2(ctx, nx, nz, L, synth.SEED_BASE + 450)
+    caps = [0, 0, 1, 2, 3, 3]
+    J = gpu_rc(ctx, nx, nz, eg, cg, 8, 3, 1e30, 6, 4, caps)
+    Jr, probes = oracle_rc(e, c, 8, 3, 1e30, 6, 4, caps)
+    assert_rel(J[:, probes], Jr[:, probes], what="J")
