@@ -435,6 +435,7 @@ def native(args):
         "gpu_launches": wl.launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    out["cascades"] = cascade_check(ctx, wl, torch, flush)
     if not args.no_populations and args.phase == "all":
         out["populations"] = population_check(ctx, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -443,6 +444,51 @@ def native(args):
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+# -------------------------------------------------------- cascade check --
+
+RC_CASCADES, RC_N0, RC_T0, RC_CAPS = 6, 4, 1.5, [0, 0, 1, 2, 3, 3]
+
+
+def cascade_check(ctx, wl, torch, flush):
+    """The paper's radiance-cascade solver around the same traversal, on the
+    benchmark's input (same grid): 6 cascades, 4 cascade-0 directions, interval
+    end 1.5, at full resolution and with VLM levels 0-3 and the per-cascade caps;
+    time per solve (CUDA events, L2 flushed between solves) and J error of the
+    accelerated cascades against the full-resolution ones at every probe."""
+    api = wl.api
+    ws = torch.empty(api.rc_workspace_floats(NX, NZ, N_LAMBDA, W, RC_N0), dtype=torch.float32, device="cuda")
+    J0 = torch.empty((N_LAMBDA, NX * NZ), dtype=torch.float32, device="cuda")
+    J1 = torch.empty_like(J0)
+    mask = (wl.grid.block_offset.view(NZ // 16, NX // 16) >= 0).repeat_interleave(16, 0).repeat_interleave(16, 1)
+    mask = mask.reshape(-1)
+
+    def timed(mp, caps, J):
+        def one(ev):
+            if ev is not None:
+                ev[0].record()
+            api.rc_solve(ctx, wl.grid, mp, RC_CASCADES, RC_N0, RC_T0, level_cap=caps, J=J, workspace=ws)
+            if ev is not None:
+                ev[1].record()
+        t, _ = time_steps(one, 3, 1, torch, flush)
+        return sum(t) / len(t)
+
+    m0 = api.mips_build(ctx, wl.grid, wl.eta, wl.chi, W, 0, 1e30, 1e30, CHI_DS_MIN)
+    t_full = timed(m0, [0] * RC_CASCADES, J0)
+    out = {"config": f"{RC_CASCADES} cascades (branching factor 2), {RC_N0} cascade-0 directions, interval end "
+                     f"{RC_T0}, per-cascade level caps {RC_CAPS}, same input and grid as the timed step",
+           "full_resolution_ms": t_full}
+    ref = J0[:, mask].double()
+    for name, iod in (("iod_1e-2", THR), ("paper_iod_1", 1.0), ("unlimited_vlm", 1e30)):
+        mp = api.mips_build(ctx, wl.grid, wl.eta, wl.chi, W, MAX_MIP, iod, iod, CHI_DS_MIN, log_mean=False)
+        t = timed(mp, RC_CAPS, J1)
+        rel = ((J1[:, mask].double() - ref).abs() / ref.abs().clamp_min(1e-30)).flatten().cpu().numpy() * 100.0
+        out[name] = {"ms": t, "speedup_vs_full_resolution": t_full / t,
+                     "j_err_pct_vs_full_resolution": {q: float(np.percentile(rel, p)) for q, p in
+                                                      (("p50", 50), ("p99", 99), ("p99.9", 99.9), ("max", 100))}}
+    ctx.check()
+    return out
 
 
 # ------------------------------------------------------ population check --
