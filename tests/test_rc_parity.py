@@ -7,7 +7,8 @@ J is compared at every cell of every non-empty block: 1e-5 relative.
 * full resolution (max MIP 0), the static line model, 4 cascades;
 * unlimited averaging with per-cascade caps [0, 0, 1, 2];
 * a random medium with transparent emitters and a boundary intensity, W = 1 and 4;
-* the paper's configuration (6 cascades, n0 = 4, t0 = 1.5, caps [0, 0, 1, 2, 3, 4]);
+* the paper's configuration (6 cascades, n0 = 4, t0 = 1.5, caps [0, 0, 1, 2, 3, 4]
+  within levels 0-3) at 128^2, 512^2 and the benchmark's 1024^2;
 * bfloat16 bricks at level 0 against the oracle on bfloat16-rounded records.
 """
 
@@ -133,6 +134,18 @@ def test_rc_paper_configuration_512(ctx):
     nx = nz = 512
     L = 8
     eg, cg, e, c = line2(ctx, nx, nz, L, synth.SEED_BASE + 450)
+    caps = [0, 0, 1, 2, 3, 3]
+    J = gpu_rc(ctx, nx, nz, eg, cg, 8, 3, 1e30, 6, 4, caps)
+    Jr, probes = oracle_rc(e, c, 8, 3, 1e30, 6, 4, caps)
+    assert_rel(J[:, probes], Jr[:, probes], what="J")
+
+
+def test_rc_bench_configuration_1024(ctx):
+    # the benchmark's cascade section at full size: its 1024^2 atmosphere (one
+    # batch of 8 wavelengths), 6 cascades, caps [0, 0, 1, 2, 3, 3], VLM 0-3 with
+    # unlimited averaging (no level decision near a threshold), every probe
+    nx = nz = 1024
+    eg, cg, e, c = line2(ctx, nx, nz, 8, synth.SEED_BASE + 2)
     caps = [0, 0, 1, 2, 3, 3]
     J = gpu_rc(ctx, nx, nz, eg, cg, 8, 3, 1e30, 6, 4, caps)
     Jr, probes = oracle_rc(e, c, 8, 3, 1e30, 6, 4, caps)
