@@ -338,13 +338,18 @@ def se_solve(ctx: Context, atom: Atom, T, ne, nh, jbar, out=None):
 
 def lambda_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, nz: int, dirs, weights,
                      n_iter: int, accelerated: bool = False, W: int = 8, max_mip: int = 3, iod: float = 1e-2,
-                     chi_ds_min: float = 0.25, band=None, pops=None, storage: int = STORE_F32):
+                     chi_ds_min: float = 0.25, band=None, pops=None, storage: int = STORE_F32,
+                     cascades: dict | None = None):
     """Fixed-length Lambda iteration: [eta, chi -> formal solution -> Jbar -> SE] x n_iter.
 
     Every step is a library call; this function only sequences them.  The plain
     variant solves at full resolution from every cell of every non-empty block
     (``dex_formal_solve_dense`` over that probe list); the accelerated one builds
     the MIP chains (records in the ``storage`` format) and runs the HDDA solve.
+    With ``cascades`` (keys ``n_cascades``, ``n0``, optional ``t0``,
+    ``level_cap``) the formal solution is the radiance-cascade solve instead
+    (``dirs``/``weights`` unused): at full resolution when not ``accelerated``,
+    else over the VLM levels with the per-cascade caps.
     Returns the float64 populations.
     """
     n = nx * nz
@@ -356,10 +361,20 @@ def lambda_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, 
     J = torch.empty_like(eta)
     jbar = None
     grid, mips, planes, probes = None, None, None, None
+    rc_ws = None
     for _ in range(n_iter):
         atom_eta_chi(ctx, atom, lam_nm, tag, T, ne, pops, eta, chi)
         grid = grid_build(ctx, nx, nz, eta, chi, out=grid)
-        if accelerated:
+        if cascades is not None:
+            C, n0 = int(cascades["n_cascades"]), int(cascades["n0"])
+            if rc_ws is None:
+                rc_ws = torch.empty(max(rc_workspace_floats(nx, nz, L, W, n0), 4), dtype=torch.float32,
+                                    device=T.device)
+            mm = max_mip if accelerated else 0
+            mips = mips_build(ctx, grid, eta, chi, W, mm, iod, iod, chi_ds_min, out=mips, storage=storage)
+            caps = cascades.get("level_cap") if accelerated else [0] * C
+            rc_solve(ctx, grid, mips, C, n0, float(cascades.get("t0", 1.5)), level_cap=caps, J=J, workspace=rc_ws)
+        elif accelerated:
             mips = mips_build(ctx, grid, eta, chi, W, max_mip, iod, iod, chi_ds_min, out=mips, storage=storage)
             formal_solve_hdda(ctx, grid, mips, dirs, weights, J=J, band=band)
         else:

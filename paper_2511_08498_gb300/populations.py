@@ -9,7 +9,12 @@ plain float32 path agrees with the float64 oracle to ~1e-5 on the reduced
 instance of the tests).  Every step is a library call; this module only
 sequences them.
 
-Usage: python -m paper_2511_08498_gb300.populations [--n 1024] [--iters 20] [--out FILE]
+With ``--cascades`` the formal solution is the radiance-cascade solve (6
+cascades, 4 cascade-0 directions, interval end 1.5; the paper's solver): full
+resolution as the reference, then VLM levels 0-3 with the per-cascade caps
+[0, 0, 1, 2, 3, 3] at IoD 1e-2, 1 and unlimited averaging.
+
+Usage: python -m paper_2511_08498_gb300.populations [--n 1024] [--iters 20] [--cascades] [--out FILE]
 """
 
 from __future__ import annotations
@@ -29,7 +34,11 @@ RUNS = [(1e-2, api.STORE_F32), (1e-2, api.STORE_F16), (1e-2, api.STORE_BF16), (1
         (1.0, api.STORE_F16), (1e30, api.STORE_F32)]
 
 
-def report(n=1024, n_iter=20, n_dir=96):
+RC = {"n_cascades": 6, "n0": 4, "t0": 1.5, "level_cap": [0, 0, 1, 2, 3, 3]}
+RC_RUNS = [(1e-2, api.STORE_F32), (1.0, api.STORE_F32), (1e30, api.STORE_F32)]
+
+
+def report(n=1024, n_iter=20, n_dir=96, cascades=False):
     import synth
     from synth.atom import line_wavelength_grid, populations_atmosphere, three_level_atom
     ctx = api.Context(0)
@@ -45,15 +54,18 @@ def report(n=1024, n_iter=20, n_dir=96):
         torch.cuda.synchronize()
         t0 = time.time()
         p = api.lambda_iteration(ctx, atom, lam, tag, dev["temperature"], dev["ne"], dev["nh"], n, n, dirs, w,
-                                 n_iter, accelerated=accelerated, iod=iod, band=BAND, storage=storage)
+                                 n_iter, accelerated=accelerated, iod=iod, band=BAND, storage=storage,
+                                 cascades=RC if cascades else None)
         ctx.check()
         return p, (time.time() - t0) / n_iter
 
     ref, t_plain = run(False)
-    out = {"workload": f"three-level atom, {n}x{n}, {lam.size} wavelengths, {n_dir} directions, {n_iter} Lambda "
-                       f"steps from LTE, VLM mip 0-3, distance limits {BAND}",
+    solver = (f"radiance cascades {RC}" if cascades else
+              f"long characteristics, {n_dir} directions, distance limits {BAND}")
+    out = {"workload": f"three-level atom, {n}x{n}, {lam.size} wavelengths, {n_iter} Lambda steps from LTE, "
+                       f"VLM mip 0-3; formal solution: {solver}",
            "plain": {"s_per_iteration": t_plain}, "accelerated": []}
-    for iod, storage in RUNS:
+    for iod, storage in (RC_RUNS if cascades else RUNS):
         p, t = run(True, iod, storage)
         e = ((p - ref).abs() / ref.abs().clamp_min(1e-300))[:, live].reshape(-1).double().cpu().numpy() * 100.0
         out["accelerated"].append({"iod": iod, "storage": ["f32", "bf16", "f16"][storage], "s_per_iteration": t,
@@ -68,9 +80,10 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=20)
+    ap.add_argument("--cascades", action="store_true")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
-    rep = report(args.n, args.iters)
+    rep = report(args.n, args.iters, cascades=args.cascades)
     s = json.dumps(rep)
     if args.out:
         with open(args.out, "w") as fh:

@@ -102,3 +102,47 @@ def test_lambda_iteration_matches_oracle(setup, accelerated):
     live = m["temperature"].reshape(-1) > 0
     err = rel(pops.cpu().numpy(), ref)[:, live]
     assert err.max() < 1e-4, f"max population error {err.max():.3e}"
+
+
+def oracle_rc_lambda_iteration(s, n_iter, C, n0, caps, accelerated, iod=1.0):
+    """The same iteration with the float64 radiance-cascade oracle as formal solution."""
+    from oracle import rc
+    ad, m, lam, tag = s["ad"], s["m"], s["lam"], s["tag"]
+    T, ne, nh = m["temperature"], m["ne"], m["nh"]
+    pops = oa.lte_populations(ad, T, nh)
+    nz, nx = T.shape
+    dirs = synth.rc_directions(n0, C)
+    for _ in range(n_iter):
+        eta, chi = oa.eta_chi(ad, lam, tag, T, ne, pops, m["cell_cm"])
+        eta = eta.astype(np.float32).astype(np.float64)
+        chi = chi.astype(np.float32).astype(np.float64)
+        empty = omips.block_empty(eta, chi, 16)
+        L = eta.shape[0]
+        if accelerated:
+            levels, passes = omips.mip_chain(eta, chi, 3, iod, iod, 0.25, mean="linear")
+            lev = omips.block_levels(passes, empty, 16, 8)
+        else:
+            levels, passes = [(eta, chi)], []
+            lev = omips.block_levels([], empty, 16, 8, n_lambda=L)
+            caps = [0] * C
+        grids = [omips.expand(levels, np.where(lev >= 0, np.minimum(lev, caps[i]), -1), 8) for i in range(C)]
+        J = rc.rc_solve(grids, C, n0, dirs)
+        J[:, ~np.repeat(np.repeat(~empty, 16, 0), 16, 1).reshape(-1)] = 0.0
+        jb = oa.jbar(ad, lam, tag, T.reshape(-1), J)
+        pops = oa.se_solve(ad, T.reshape(-1), ne.reshape(-1), nh.reshape(-1), jb).reshape((3,) + T.shape)
+    return pops.reshape(3, -1)
+
+
+@pytest.mark.parametrize("accelerated", [False, True])
+def test_cascade_lambda_iteration_matches_oracle(setup, accelerated):
+    s = setup
+    api, ctx, dev, m = s["api"], s["ctx"], s["dev"], s["m"]
+    C, n0, caps, n_iter = 4, 4, [0, 0, 1, 2], 10
+    pops = api.lambda_iteration(ctx, s["atom"], s["lam"], s["tag"], dev["temperature"], dev["ne"], dev["nh"], 48, 48,
+                                None, None, n_iter, accelerated=accelerated, iod=1.0,
+                                cascades={"n_cascades": C, "n0": n0, "level_cap": caps})
+    ctx.check()
+    ref = oracle_rc_lambda_iteration(s, n_iter, C, n0, caps, accelerated)
+    live = m["temperature"].reshape(-1) > 0
+    err = rel(pops.cpu().numpy(), ref)[:, live]
+    assert err.max() < 1e-4, f"max population error {err.max():.3e}"
