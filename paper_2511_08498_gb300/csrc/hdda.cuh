@@ -169,7 +169,12 @@ __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const H
 
     const int blk0 = P.active[a0];
     const int bx0 = blk0 % P.nbx, bz0 = blk0 / P.nbx;
-    const int i = bx0 * DEX_BLOCK + (tid & 15), j = bz0 * DEX_BLOCK + (tid >> 4);
+    // warp w covers an 8 x 4 tile of the block (lanes along x, then z): a warp's rays
+    // meet x faces in at most 8 different iterations (16 with whole 16-cell rows),
+    // while its record loads stay within the block's brick
+    const int wrp = tid >> 5;
+    const int i = bx0 * DEX_BLOCK + (wrp & 1) * 8 + (tid & 7);
+    const int j = bz0 * DEX_BLOCK + (wrp >> 1) * 4 + ((tid & 31) >> 3);
     const int state0 = block_state(s_words, blk0) - 1;
     if (state0 < 0) {  // state words do not describe this active block
         raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);

@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(256) k_batch_solve(const BatchParams P)
 
         const int blk0 = A.active[r];
         const int bx0 = blk0 % A.nbx, bz0 = blk0 / A.nbx;
-        const int i = bx0 * DEX_BLOCK + (tid & 15), j = bz0 * DEX_BLOCK + (tid >> 4);
+        // warp w: an 8 x 4 tile of the block (the probe order of k_solve_hdda_t)
+        const int i = bx0 * DEX_BLOCK + ((tid >> 5) & 1) * 8 + (tid & 7);
+        const int j = bz0 * DEX_BLOCK + (tid >> 6) * 4 + ((tid & 31) >> 3);
         const int state0 = block_state(s_words, blk0) - 1;
         if (state0 < 0) {
             capped = true;
