@@ -92,6 +92,11 @@ const char* dex_last_error(const dex_ctx* ctx);
  * intensity to float32 precision for eta <= 2^36 (larger values are rejected
  * with DEX_ERR_NUMERIC).  eta = chi = 0 is stored as S = chi = 0.  Wavelengths
  * beyond n_lambda are zero.  One record is 8*W bytes (W = 8: one 64-byte unit).
+ *
+ * Alignment: for W = 8 the float32 records (planes and bricks) and the bfloat16
+ * bricks are read with 256-bit loads, so those arrays must be 32-byte aligned;
+ * otherwise 16-byte (W = 1: 8-byte) alignment suffices.  A misaligned array is
+ * rejected with DEX_ERR_ARG before anything is enqueued.
  */
 
 /*
@@ -206,7 +211,7 @@ typedef struct {
  *   params            host pointer
  *   level_cap         device [nbz * nbx] per-block upper bound on the level, or NULL
  *   bricks            device [n_batch][capacity][chain][record] output records (format
- *                     params->storage):
+ *                     params->storage; alignment as for the planes above):
  *                     level m of a block starts at record sum_{k<m} (16 >> k)^2 and
  *                     is row-major over its (16 >> m)^2 voxels
  *   state_words       device [n_batch][dex_state_words] output (zeroed by the call):

@@ -50,6 +50,13 @@ int bind(dex_ctx* ctx)
 bool valid_W(int W) { return W == 1 || W == 2 || W == 4 || W == 8; }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+// Alignment the record loads need: W = 8 float32 (64-byte) and bfloat16 (32-byte)
+// records are read with 256-bit loads; other records with 128-bit (W = 1: 64-bit) loads.
+size_t rec_align(int W, int storage)
+{
+    if (W == 8 && (storage == DEX_STORE_F32 || storage == DEX_STORE_BF16)) return 32;
+    return W == 1 ? 8 : 16;
+}
 
 int fill_quadrature(dex_ctx* ctx, int n_dir, const float* dirs, const float* weights, dex::Quadrature& q)
 {
@@ -232,7 +239,8 @@ int dex_pack_planes(dex_ctx* ctx, int n_cells, int n_lambda, int W, const float*
     if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
     if (n_cells == 0 || n_lambda == 0) return ok(ctx);
     if (!eta || !chi || !planes) return fail(ctx, DEX_ERR_ARG, "null buffer");
-    if (!aligned(planes, 8 * (W < 2 ? 1 : 2))) return fail(ctx, DEX_ERR_ARG, "planes must be 16-byte aligned");
+    if (!aligned(planes, rec_align(W, DEX_STORE_F32)))
+        return fail(ctx, DEX_ERR_ARG, "planes must be %zu-byte aligned", rec_align(W, DEX_STORE_F32));
     if (int r = bind(ctx)) return r;
     cudaError_t e = dex::launch_pack_planes(ctx->stream, n_cells, n_lambda, W, eta, chi, planes, ctx->status);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "pack_planes launch");
@@ -261,7 +269,8 @@ int dex_formal_solve_dense(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, co
     if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
     if (n_lambda == 0 || n_probe == 0) return ok(ctx);
     if (!planes || !J) return fail(ctx, DEX_ERR_ARG, "planes and J are required");
-    if (!aligned(planes, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "planes misaligned");
+    if (!aligned(planes, rec_align(W, DEX_STORE_F32)))
+        return fail(ctx, DEX_ERR_ARG, "planes must be %zu-byte aligned", rec_align(W, DEX_STORE_F32));
     P.nx = nx;
     P.nz = nz;
     P.n_lambda = n_lambda;
@@ -367,7 +376,8 @@ int dex_mips_build(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, const floa
     const int nb = (nx / DEX_BLOCK) * (nz / DEX_BLOCK);
     if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
     if (!eta || !chi || !active || !n_active || !bricks || !state_words) return fail(ctx, DEX_ERR_ARG, "null buffer");
-    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    if (!aligned(bricks, rec_align(W, params->storage)))
+        return fail(ctx, DEX_ERR_ARG, "bricks must be %zu-byte aligned", rec_align(W, params->storage));
     dex::MipParams P{};
     P.nx = nx;
     P.nz = nz;
@@ -430,7 +440,8 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
     if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
         return fail(ctx, DEX_ERR_ARG, "null buffer");
-    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    const size_t ral = kind == 0 ? rec_align(W, storage) : (W == 1 ? 8 : 16);
+    if (!aligned(bricks, ral)) return fail(ctx, DEX_ERR_ARG, "bricks must be %zu-byte aligned", ral);
     P.nx = nx;
     P.nz = nz;
     P.nbx = nx / DEX_BLOCK;
@@ -807,7 +818,8 @@ static int fill_batch(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W
         if (!it.bricks || !it.state_words || !it.block_offset || !it.active || !it.n_active || !it.dirs ||
             !it.weights || !it.J)
             return fail(ctx, DEX_ERR_ARG, "atmosphere %d: null buffer", a);
-        if (!aligned(it.bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bricks misaligned", a);
+        if (!aligned(it.bricks, rec_align(W, DEX_STORE_F32)))
+            return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bricks must be %zu-byte aligned", a, rec_align(W, DEX_STORE_F32));
         if (it.n_band > 4) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: at most 4 distance thresholds", a);
         if (!std::isfinite(it.i_bc)) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: i_bc not finite", a);
         dex::AtmDesc& A = P.atm[a];
@@ -1037,7 +1049,8 @@ int dex_formal_solve_dense3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, 
     if (int r = fill_quadrature3(ctx, n_dir, dirs, weights, P.quad)) return r;
     if (n_lambda == 0 || n_probe == 0) return ok(ctx);
     if (!planes || !J) return fail(ctx, DEX_ERR_ARG, "planes and J are required");
-    if (!aligned(planes, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "planes misaligned");
+    if (!aligned(planes, rec_align(W, DEX_STORE_F32)))
+        return fail(ctx, DEX_ERR_ARG, "planes must be %zu-byte aligned", rec_align(W, DEX_STORE_F32));
     P.nx = nx;
     P.ny = ny;
     P.nz = nz;
@@ -1112,7 +1125,8 @@ int dex_mips3_build(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, c
     const long long nb = (long long)(nx / DEX_BLOCK3) * (ny / DEX_BLOCK3) * (nz / DEX_BLOCK3);
     if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %lld]", nb);
     if (!eta || !chi || !active || !n_active || !bricks || !state_words) return fail(ctx, DEX_ERR_ARG, "null buffer");
-    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    if (!aligned(bricks, rec_align(W, params->storage)))
+        return fail(ctx, DEX_ERR_ARG, "bricks must be %zu-byte aligned", rec_align(W, params->storage));
     dex::Mip3Params P{};
     P.nx = nx;
     P.ny = ny;
@@ -1176,7 +1190,8 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
     if (int r = fill_quadrature3(ctx, n_dir, dirs, weights, P.quad)) return r;
     if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
         return fail(ctx, DEX_ERR_ARG, "null buffer");
-    if (!aligned(bricks, W == 1 ? 8 : 16)) return fail(ctx, DEX_ERR_ARG, "bricks misaligned");
+    if (!aligned(bricks, rec_align(W, storage)))
+        return fail(ctx, DEX_ERR_ARG, "bricks must be %zu-byte aligned", rec_align(W, storage));
     P.nx = nx;
     P.ny = ny;
     P.nz = nz;
@@ -1249,7 +1264,8 @@ int dex_rc_solve(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip,
     if (capacity < 0 || capacity > nb) return fail(ctx, DEX_ERR_ARG, "capacity must be in [0, %d]", nb);
     if (!bricks || !state_words || !block_offset || !dirs || !workspace || !J)
         return fail(ctx, DEX_ERR_ARG, "null buffer");
-    if (!aligned(bricks, W == 1 ? 8 : 16) || !aligned(workspace, 16)) return fail(ctx, DEX_ERR_ARG, "misaligned buffer");
+    if (!aligned(bricks, rec_align(W, storage)) || !aligned(workspace, 16))
+        return fail(ctx, DEX_ERR_ARG, "misaligned buffer (bricks %zu-byte, workspace 16-byte)", rec_align(W, storage));
     dex::RcParams P{};
     P.nx = nx;
     P.nz = nz;

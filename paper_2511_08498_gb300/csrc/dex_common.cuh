@@ -160,6 +160,23 @@ __device__ __forceinline__ float plane_lo(float P, const AxisParam& a, float hi)
     return fmaf(P, a.il, fmaf(P, a.ih, -hi));
 }
 
+// 256-bit global loads (sm_100 and later): one 32-byte access per lane, so a
+// warp reading 32 neighbouring 64-byte records touches each 32-byte sector once
+// (four 128-bit loads touch every sector twice).  p must be 32-byte aligned.
+__device__ __forceinline__ void ldg256(const float* __restrict__ p, float* v)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+        : "l"(p));
+}
+
+__device__ __forceinline__ void ldg256u(const void* __restrict__ p, unsigned int* v)
+{
+    asm("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+        : "l"(p));
+}
+
 // Loads of one wavelength-batch record (2W floats, 8W-byte aligned).
 template <int W>
 struct Record {
@@ -206,7 +223,20 @@ struct RecFmt;
 template <int W>
 struct RecFmt<W, kStoreF32> {
     static constexpr int kStride = 2 * W;  // floats
-    __device__ __forceinline__ static Record<W> load(const float* p) { return load_record<W>(p); }
+    // W = 8 and kWide: two 256-bit loads (the record must be 32-byte aligned);
+    // otherwise load_record (128-bit loads)
+    template <bool kWide = true>
+    __device__ __forceinline__ static Record<W> load(const float* p)
+    {
+        if constexpr (W == 8 && kWide) {
+            Record<W> r;
+            ldg256(p, r.S);
+            ldg256(p + 8, r.chi);
+            return r;
+        } else {
+            return load_record<W>(p);
+        }
+    }
     __device__ __forceinline__ static void store(float* rec, const float* S, const float* chi)
     {
         if constexpr (W >= 2) {
@@ -228,12 +258,15 @@ struct RecFmt<W, kStoreBF16> {
     static constexpr int kStride = W;  // floats (2W bfloat16)
     __device__ __forceinline__ static float lo(unsigned int u) { return __uint_as_float(u << 16); }
     __device__ __forceinline__ static float hi(unsigned int u) { return __uint_as_float(u & 0xffff0000u); }
+    template <bool kWide = true>
     __device__ __forceinline__ static Record<W> load(const float* p)
     {
         Record<W> r;
         const uint4* q = reinterpret_cast<const uint4*>(p);
         unsigned int u[W];
-        if constexpr (W == 8) {
+        if constexpr (W == 8 && kWide) {
+            ldg256u(p, u);  // one 256-bit load (the record must be 32-byte aligned)
+        } else if constexpr (W == 8) {
             const uint4 a = __ldg(q), b = __ldg(q + 1);
             u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w; u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
         } else {
@@ -273,6 +306,7 @@ struct RecFmt<W, kStoreF16> {
     {
         return __half2float(__ushort_as_half((unsigned short)(hi_half ? (u >> 16) : (u & 0xffffu))));
     }
+    template <bool kWide = true>  // 48-byte records: 128-bit loads only
     __device__ __forceinline__ static Record<W> load(const float* p)
     {
         Record<W> r;

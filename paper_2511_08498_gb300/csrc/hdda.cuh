@@ -13,21 +13,25 @@ __host__ __device__ constexpr int level_offset(int m) { return 341 - (341 >> (2 
 struct Geo {
     int nx, nz, nbx, nbz, chain, cap_active;
     const float* batch_base;   // bricks of the wavelength batch being solved
-    const int* block_offset;
-    int n_band;                // < 0: no distance limit
-    float band[4];
+    float band[4];             // distance thresholds, padded (see set_bands)
 };
 
-// Highest level a block first entered at ray parameter t may use: with
-// distance limits, the number of thresholds band[m-1] <= t (Section 4.1: the
-// near field at full resolution, coarser levels only further out).
+// Distance thresholds of levels 1..4 padded to four: +inf for the levels beyond
+// the n_band given (never reached), 0 for all four when there is no limit
+// (n_band < 0: every level allowed from t = 0).
+__device__ __forceinline__ void set_bands(Geo& G, int n_band, const float* band)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        G.band[q] = n_band < 0 ? 0.0f : (q < n_band ? band[q] : __int_as_float(0x7f800000));
+}
+
+// Highest level a block first entered at ray parameter t >= 0 may use: the
+// number of thresholds band[m-1] <= t (Section 4.1: the near field at full
+// resolution, coarser levels only further out).
 __device__ __forceinline__ int distance_cap(const Geo& G, float t)
 {
-    if (G.n_band < 0) return 4;
-    int m = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) m += (q < G.n_band && G.band[q] <= t) ? 1 : 0;
-    return m;
+    return (G.band[0] <= t) + (G.band[1] <= t) + (G.band[2] <= t) + (G.band[3] <= t);
 }
 
 __device__ __forceinline__ int block_state(const unsigned long long* words, int blk)
@@ -36,18 +40,44 @@ __device__ __forceinline__ int block_state(const unsigned long long* words, int 
     return (int)((words[wi] >> sh) & 7ull);
 }
 
+// Block lookups of the traversal: key(blk) once per block entered, then its
+// state (0 = empty, level + 1) and, for non-empty blocks, its brick offset.
+//
+// WordLookup: the packed 3-bit states (staged in shared memory) and the global
+// offset table, read only for non-empty blocks.
+struct WordLookup {
+    const unsigned long long* words;
+    const int* offset;
+    __device__ __forceinline__ int key(int blk) const { return blk; }
+    __device__ __forceinline__ int state(int k) const { return block_state(words, k); }
+    __device__ __forceinline__ int offset_of(int k) const { return offset[k]; }
+};
+
+// InfoLookup: one shared-memory word per block, offset * 8 + state (offset -1
+// for empty blocks), so a block crossing costs one shared load.
+struct InfoLookup {
+    const int* info;
+    __device__ __forceinline__ int key(int blk) const { return info[blk]; }
+    __device__ __forceinline__ int state(int k) const { return k & 7; }
+    __device__ __forceinline__ int offset_of(int k) const { return k >> 3; }
+};
+
+// Grids of at most this many blocks stage the one-word-per-block table (32 KB).
+constexpr int kInfoMaxBlocks = 8192;
+
+__device__ __forceinline__ int pack_block_info(int offset, int state) { return offset * 8 + state; }
+
 // Voxel models: Model::kStride floats per voxel record, Model::kPerBatch whether
 // records differ per wavelength batch, Model::Voxel / load / integrate the
 // per-segment update of the W wavelengths of batch b along propagation (wx, wz).
 //
 // One ray from the centre of cell (i, j) (in active block a0 = (bx0, bz0), whose
 // level is mip0) along d = (dx, dz): accumulates I and T (initialised by the
-// caller) over the traversal; s_words holds the batch's packed block states.
-template <int W, bool COUNT, class Model>
+// caller) over the traversal; L looks up the batch's block states and offsets.
+template <int W, bool COUNT, class Model, class Lookup>
 __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Params& M, int b, int i, int j,
                                           int bx0, int bz0, int a0, int mip0, float dx, float dz,
-                                          const unsigned long long* __restrict__ s_words, float* I, float* T,
-                                          unsigned int& nseg, bool& capped)
+                                          const Lookup& L, float* I, float* T, unsigned int& nseg, bool& capped)
 {
     constexpr int REC = Model::kStride;
     const float* __restrict__ batch_base = G.batch_base;
@@ -62,6 +92,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
 
     // tracer state: level, voxel size, block, block-local voxel, far-face plane offsets
     int mip = mip0, vox = 1 << mip0, side = DEX_BLOCK >> mip0;
+    float fvox = (float)vox;
     int bxc = bx0, bzc = bz0;
     int lx = (i - bx0 * DEX_BLOCK) >> mip, lz = (j - bz0 * DEX_BLOCK) >> mip;
     float Px = (float)(bx0 * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
@@ -81,7 +112,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
         const float* cur_rp = rp;
         if (!last) {
             if (it >= cap) { capped = true; break; }
-            const float fv = (float)vox;
+            const float fv = fvox;
             bool cross;
             if (on_x) {
                 lx += sx;
@@ -104,8 +135,8 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
                     capped = true;
                     break;
                 }
-                const int blk = bzn * G.nbx + bxn;
-                const int st = block_state(s_words, blk) - 1;
+                const int key = L.key(bzn * G.nbx + bxn);
+                const int st = L.state(key) - 1;
                 const int mip_new = st < 0 ? -1 : min(st, distance_cap(G, th));
                 if (mip_new == mip) {
                     if (on_x) lx = negx ? side - 1 : 0;
@@ -127,6 +158,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
                     mip = mip_new;
                     const int shift = mip >= 0 ? mip : 4;
                     vox = 1 << shift;
+                    fvox = (float)vox;
                     side = DEX_BLOCK >> shift;
                     lx = (m0x - bxn * DEX_BLOCK) >> shift;
                     lz = (m0z - bzn * DEX_BLOCK) >> shift;
@@ -136,7 +168,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
                 bxc = bxn;
                 bzc = bzn;
                 if (mip >= 0) {
-                    const int a = G.block_offset[blk];
+                    const int a = L.offset_of(key);
                     rp = batch_base + ((size_t)a * G.chain + level_offset(mip) + lz * side + lx) * REC;
                 }
             }
@@ -153,16 +185,26 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
     }
 }
 
-template <int W, bool COUNT, class Model>
+// kInfo: the CTA stages one word per block (offset * 8 + state, InfoLookup;
+// dynamic shared memory 4 * nbx * nbz bytes, grids of at most kInfoMaxBlocks
+// blocks); otherwise the packed state words (WordLookup; 8 * n_words bytes).
+template <int W, bool COUNT, class Model, bool kInfo = false>
 __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const HddaParams P, const typename Model::Params M)
 {
-    extern __shared__ unsigned long long s_words[];
+    extern __shared__ unsigned long long s_dyn[];
     __shared__ float s_J[W][256];
     const int a0 = blockIdx.x;
     if (a0 >= *P.n_active) return;
     const int b = blockIdx.y;
     const int tid = threadIdx.x;
-    for (int q = tid; q < P.n_words; q += blockDim.x) s_words[q] = P.words[(size_t)b * P.n_words + q];
+    const unsigned long long* words_b = P.words + (size_t)b * P.n_words;
+    int* s_info = reinterpret_cast<int*>(s_dyn);
+    if constexpr (kInfo) {
+        const int n_blocks = P.nbx * P.nbz;
+        for (int q = tid; q < n_blocks; q += blockDim.x) s_info[q] = pack_block_info(P.block_offset[q], block_state(words_b, q));
+    } else {
+        for (int q = tid; q < P.n_words; q += blockDim.x) s_dyn[q] = words_b[q];
+    }
 #pragma unroll
     for (int w = 0; w < W; ++w) s_J[w][tid] = 0.0f;
     __syncthreads();
@@ -175,7 +217,7 @@ __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const H
     const int wrp = tid >> 5;
     const int i = bx0 * DEX_BLOCK + (wrp & 1) * 8 + (tid & 7);
     const int j = bz0 * DEX_BLOCK + (wrp >> 1) * 4 + ((tid & 31) >> 3);
-    const int state0 = block_state(s_words, blk0) - 1;
+    const int state0 = (kInfo ? (s_info[blk0] & 7) : block_state(s_dyn, blk0)) - 1;
     if (state0 < 0) {  // state words do not describe this active block
         raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
         return;
@@ -188,10 +230,7 @@ __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const H
     G.chain = P.chain;
     G.cap_active = P.cap_active;
     G.batch_base = P.bricks + (Model::kPerBatch ? (size_t)b * P.cap_active * P.chain * Model::kStride : (size_t)0);
-    G.block_offset = P.block_offset;
-    G.n_band = P.n_band;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) G.band[q] = P.band[q];
+    set_bands(G, P.n_band, P.band);
     const int mip0 = min(state0, distance_cap(G, 0.0f));
     unsigned int nseg = 0;
     bool capped = false;
@@ -201,7 +240,12 @@ __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const H
         float I[W], T[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
-        trace_ray<W, COUNT, Model>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz, s_words, I, T, nseg, capped);
+        if constexpr (kInfo)
+            trace_ray<W, COUNT, Model>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz, InfoLookup{s_info}, I, T, nseg,
+                                       capped);
+        else
+            trace_ray<W, COUNT, Model>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz,
+                                       WordLookup{s_dyn, P.block_offset}, I, T, nseg, capped);
         const float wk = P.quad.w[k];
 #pragma unroll
         for (int w = 0; w < W; ++w) {

@@ -36,7 +36,7 @@ struct StaticRec {
         int unused;
     };
     using Voxel = Record<W>;
-    __device__ __forceinline__ static Voxel load(const float* p) { return load_record<W>(p); }
+    __device__ __forceinline__ static Voxel load(const float* p) { return RecFmt<W, kStoreF32>::load(p); }
     __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
                                                      float* I, float* T)
     {
@@ -102,18 +102,15 @@ __global__ void __launch_bounds__(256) k_batch_solve(const BatchParams P)
         G.chain = A.chain;
         G.cap_active = A.cap_active;
         G.batch_base = A.bricks + (size_t)b * A.cap_active * A.chain * (2 * W);
-        G.block_offset = A.block_offset;
-        G.n_band = A.n_band;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) G.band[q] = A.band[q];
+        set_bands(G, A.n_band, A.band);
         const int mip0 = min(state0, distance_cap(G, 0.0f));
         typename StaticRec<W>::Params M{};
         for (int k = 0; k < A.n_dir; ++k) {
             float I[W], T[W];
 #pragma unroll
             for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
-            trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k], s_words, I, T,
-                                               nseg_unused, capped);
+            trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
+                                               WordLookup{s_words, A.block_offset}, I, T, nseg_unused, capped);
             const float wk = s_w[k];
 #pragma unroll
             for (int w = 0; w < W; ++w) s_J[w][tid] = fmaf(wk, fmaf(T[w], A.i_bc, I[w]), s_J[w][tid]);

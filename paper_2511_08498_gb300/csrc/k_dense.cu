@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
                 capped = true;
                 break;
             }
-            const Record<W> r = load_record<W>(rp);
+            const Record<W> r = RecFmt<W, kStoreF32>::load(rp);
             const float nl2 = len * kNegLog2e;
             segments<W>(r.S, r.chi, nl2, I, T);
             if (COUNT) nseg += (th > th_prev);

@@ -62,28 +62,44 @@ cudaError_t launch_hdda_kernel(K kernel, dim3 grid, size_t smem, cudaStream_t s,
 cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& P)
 {
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
-    const size_t smem = sizeof(unsigned long long) * (size_t)P.n_words;
+    // W = 8 on grids of at most kInfoMaxBlocks blocks: one shared-memory word per
+    // block (InfoLookup); otherwise the packed state words (WordLookup)
+    const long long n_blocks = (long long)P.nbx * P.nbz;
+    const bool info = P.W == 8 && n_blocks <= kInfoMaxBlocks;
+    const size_t smem = info ? sizeof(int) * (size_t)n_blocks : sizeof(unsigned long long) * (size_t)P.n_words;
     dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
     cudaError_t e = cudaSuccess;
     switch (P.W * 4 + P.storage) {
+#define MP_(WW, ST) typename StaticModel<WW, ST>::Params{}
 #define DEX_LAUNCH(WW, ST)                                                                                   \
     case WW * 4 + ST:                                                                                        \
         if (P.seg_count)                                                                                     \
-            e = launch_hdda_kernel(k_solve_hdda_t<WW, true, StaticModel<WW, ST>>, grid, smem, s, P,          \
-                                   typename StaticModel<WW, ST>::Params{});                                  \
+            e = launch_hdda_kernel(k_solve_hdda_t<WW, true, StaticModel<WW, ST>>, grid, smem, s, P, MP_(WW, ST));   \
         else                                                                                                 \
-            e = launch_hdda_kernel(k_solve_hdda_t<WW, false, StaticModel<WW, ST>>, grid, smem, s, P,         \
-                                   typename StaticModel<WW, ST>::Params{});                                  \
+            e = launch_hdda_kernel(k_solve_hdda_t<WW, false, StaticModel<WW, ST>>, grid, smem, s, P, MP_(WW, ST));  \
+        break;
+#define DEX_LAUNCH_INFO(ST)                                                                                  \
+    case 8 * 4 + ST:                                                                                         \
+        if (info && P.seg_count)                                                                             \
+            e = launch_hdda_kernel(k_solve_hdda_t<8, true, StaticModel<8, ST>, true>, grid, smem, s, P, MP_(8, ST));  \
+        else if (info)                                                                                       \
+            e = launch_hdda_kernel(k_solve_hdda_t<8, false, StaticModel<8, ST>, true>, grid, smem, s, P, MP_(8, ST)); \
+        else if (P.seg_count)                                                                                \
+            e = launch_hdda_kernel(k_solve_hdda_t<8, true, StaticModel<8, ST>>, grid, smem, s, P, MP_(8, ST));     \
+        else                                                                                                 \
+            e = launch_hdda_kernel(k_solve_hdda_t<8, false, StaticModel<8, ST>>, grid, smem, s, P, MP_(8, ST));    \
         break;
         DEX_LAUNCH(1, kStoreF32)
         DEX_LAUNCH(2, kStoreF32)
         DEX_LAUNCH(4, kStoreF32)
-        DEX_LAUNCH(8, kStoreF32)
+        DEX_LAUNCH_INFO(kStoreF32)
         DEX_LAUNCH(4, kStoreBF16)
-        DEX_LAUNCH(8, kStoreBF16)
+        DEX_LAUNCH_INFO(kStoreBF16)
         DEX_LAUNCH(4, kStoreF16)
-        DEX_LAUNCH(8, kStoreF16)
+        DEX_LAUNCH_INFO(kStoreF16)
+#undef DEX_LAUNCH_INFO
 #undef DEX_LAUNCH
+#undef MP_
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

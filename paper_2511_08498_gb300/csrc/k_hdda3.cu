@@ -157,7 +157,7 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
             }
         }
         if (cur_mip >= 0) {
-            const Record<W> r = RecFmt<W, ST>::load(cur_rp);
+            const Record<W> r = RecFmt<W, ST>::template load<false>(cur_rp);
             segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
             if (COUNT) nseg += (th > th_prev);
         }

@@ -118,3 +118,81 @@ def test_one_wavelength_in_a_batch_of_eight(ctx):
     Ja, _ = accelerated(ctx, nx, nz, eg, cg, 8, 2, 1e30, dirs, w, [6.0, 24.0])
     probes, Jr, _ = oracle_accelerated(er, cr, 8, 2, 1e30, dirs, w, [6.0, 24.0])
     assert rel(Ja[:, probes], Jr).max() < 1e-5
+
+
+def test_misaligned_records_rejected(ctx):
+    """W = 8 float32 and bfloat16 records are read with 256-bit loads: planes and bricks
+    must be 32-byte aligned, and a 16-byte-aligned view is refused before any launch."""
+    from paper_2511_08498_gb300 import api
+    from paper_2511_08498_gb300._native import DexError
+    nx, nz, L = 64, 48, 8
+    eg, cg, _, _ = line_case(ctx, nx, nz, L, synth.SEED_BASE + 730)
+    dirs, w = synth.directions(8)
+    n = api.planes_floats(nx * nz, L, 8)
+    buf = torch.zeros(n + 8, dtype=torch.float32, device="cuda")
+    assert buf.data_ptr() % 32 == 0
+    with pytest.raises(DexError, match="aligned"):
+        api.pack_planes(ctx, eg, cg, 8, out=buf[4:4 + n].view(-1, nx * nz, 16))
+    planes = api.pack_planes(ctx, eg, cg, 8, out=buf[8:8 + n].view(-1, nx * nz, 16))  # 32-byte offset: accepted
+    J, _, _ = api.formal_solve_dense(ctx, nx, nz, L, 8, planes, dirs, w)
+    with pytest.raises(DexError, match="aligned"):
+        api.formal_solve_dense(ctx, nx, nz, L, 8, buf[4:4 + n].view(-1, nx * nz, 16), dirs, w)
+    grid = api.grid_build(ctx, nx, nz, eg, cg)
+    mips = api.mips_build(ctx, grid, eg, cg, 8, 3, 1e-2, 1e-2, 0.25, log_mean=False)
+    nb = mips.bricks.numel()
+    shifted = torch.empty(nb + 4, dtype=torch.float32, device="cuda")
+    shifted[4:].copy_(mips.bricks.reshape(-1))
+    good = mips.bricks
+    mips.bricks = shifted[4:]
+    with pytest.raises(DexError, match="aligned"):
+        api.formal_solve_hdda(ctx, grid, mips, dirs, w)
+    mips.bricks = good
+    api.formal_solve_hdda(ctx, grid, mips, dirs, w)
+    ctx.check()
+    # W = 4 records keep the 16-byte rule
+    n4 = api.planes_floats(nx * nz, L, 4)
+    p4 = api.pack_planes(ctx, eg, cg, 4, out=buf[4:4 + n4].view(-1, nx * nz, 8))
+    J4, _, _ = api.formal_solve_dense(ctx, nx, nz, L, 4, p4, dirs, w)
+    ctx.check()
+    assert torch.equal(J4, J)
+
+
+def test_grid_above_the_staged_block_table(ctx):
+    """W = 8 grids of more than 8192 blocks read block states from the packed words and
+    offsets from global memory instead of one staged word per block: accelerated
+    solve of a 65536 x 48 grid (12288 blocks) with empty blocks and distance-limited
+    levels against the oracle at sampled probes."""
+    from paper_2511_08498_gb300 import api
+    nx, nz, L, W = 65536, 48, 2, 8
+    rng = np.random.default_rng(synth.SEED_BASE + 740)
+    x = np.arange(nx)[None, None, :] + 0.5
+    z = np.arange(nz)[None, :, None] + 0.5
+    chi = (0.05 * (1.5 + np.sin(2 * np.pi * x / 700.0)) * np.exp(-z / 40.0)
+           * np.array([1.0, 3.0])[:, None, None]).astype(np.float32)
+    chi = np.broadcast_to(chi, (L, nz, nx)).copy()
+    eta = (chi * (1.0 + 0.5 * np.cos(2 * np.pi * x / 333.0))).astype(np.float32)
+    nbx = nx // 16
+    blk = np.arange(nbx)
+    empty_cols = (blk % 7 == 3) | (rng.random(nbx) < 0.1)
+    for bz in range(nz // 16):
+        cols = empty_cols if bz != 1 else (blk % 11 == 5)
+        for bx in np.nonzero(cols)[0]:
+            chi[:, bz * 16:(bz + 1) * 16, bx * 16:(bx + 1) * 16] = 0.0
+            eta[:, bz * 16:(bz + 1) * 16, bx * 16:(bx + 1) * 16] = 0.0
+    eg = torch.from_numpy(eta.reshape(L, -1)).cuda()
+    cg = torch.from_numpy(chi.reshape(L, -1)).cuda()
+    dirs, w = synth.directions(8)
+    band = [6.0, 24.0, 96.0]
+    grid = api.grid_build(ctx, nx, nz, eg, cg)
+    assert grid.n_blocks > 8192
+    mips = api.mips_build(ctx, grid, eg, cg, W, 3, 1e30, 1e30, 0.25, log_mean=False)
+    J, _, _ = api.formal_solve_hdda(ctx, grid, mips, dirs, w, band=band)
+    ctx.check()
+    er, cr = eta.astype(np.float64), chi.astype(np.float64)
+    levels, passes = omips.mip_chain(er, cr, 3, 1e30, 1e30, 0.25, mean="linear")
+    empty = omips.block_empty(er, cr, 16)
+    lev = omips.block_levels(passes, empty, 16, W, n_lambda=L)
+    all_probes = omips.probes_of_blocks(empty, 16)
+    probes = np.sort(rng.choice(all_probes, 4096, replace=False)).astype(np.int32)
+    Jr = lc.formal_solve_banded(levels, lev, 16, W, band, dirs, w, probes)
+    assert rel(J.cpu().numpy()[:, probes], Jr).max() < 1e-5
