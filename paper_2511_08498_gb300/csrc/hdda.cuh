@@ -68,7 +68,8 @@ constexpr int kInfoMaxBlocks = 8192;
 __device__ __forceinline__ int pack_block_info(int offset, int state) { return offset * 8 + state; }
 
 // Voxel models: Model::kStride floats per voxel record, Model::kPerBatch whether
-// records differ per wavelength batch, Model::Voxel / load / integrate the
+// records differ per wavelength batch, Model::kEarlyLoad whether the record is
+// loaded at the top of each step, Model::Voxel / load / integrate the
 // per-segment update of the W wavelengths of batch b along propagation (wx, wz).
 //
 // One ray from the centre of cell (i, j) (in active block a0 = (bx0, bz0), whose
@@ -102,6 +103,11 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
     typename Model::Voxel cur;
 
     for (int it = 0;; ++it) {
+        // models with kEarlyLoad issue the current voxel's record before the
+        // stepping and crossing bookkeeping, which then hides its latency
+        if constexpr (Model::kEarlyLoad) {
+            if (mip >= 0) cur = Model::load(rp);
+        }
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
         const float th = on_x ? tnx : tnz;
@@ -174,7 +180,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
             }
         }
         if (cur_mip >= 0) {
-            cur = Model::load(cur_rp);
+            if constexpr (!Model::kEarlyLoad) cur = Model::load(cur_rp);
             const float nl2 = len * kNegLog2e;
             Model::integrate(M, cur, b, -dx, -dz, nl2, I, T);
             if (COUNT) nseg += (th > th_prev);

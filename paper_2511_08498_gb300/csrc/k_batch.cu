@@ -32,6 +32,7 @@ __device__ __forceinline__ unsigned long long global_ns()
 template <int W>
 struct StaticRec {
     static constexpr int kStride = 2 * W;
+    static constexpr bool kEarlyLoad = true;  // as the float32 static model of the single-grid solve
     struct Params {
         int unused;
     };

@@ -56,6 +56,7 @@ struct CavMlpModel {
     static constexpr int kStride = kCavStride;
     static constexpr bool kPerBatch = false;
     static constexpr int kMinBlocks = 1;  // the network's 64 hidden values stay in registers
+    static constexpr bool kEarlyLoad = false;
     using Params = CavMlpParams;
     struct Voxel {
         float p[kCavStride];
@@ -93,6 +94,7 @@ struct CavModel {
     static constexpr int kStride = kCavStride;
     static constexpr bool kPerBatch = false;
     static constexpr int kMinBlocks = 4;
+    static constexpr bool kEarlyLoad = false;
     using Params = CavParams;
     struct Voxel {
         float p[kCavStride];

@@ -108,6 +108,12 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
 #pragma unroll
         for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
         for (int it = 0;; ++it) {
+            if (it >= cap || (unsigned)ci >= (unsigned)P.nx || (unsigned)cj >= (unsigned)P.nz) {
+                capped = true;
+                break;
+            }
+            // the record is issued first: the plane arithmetic below hides its latency
+            const Record<W> r = RecFmt<W, kStoreF32>::load(rp);
             const float tnx = Px * ax.ih, tnz = Pz * az.ih;
             const bool on_x = tnx <= tnz;
             const float th = on_x ? tnx : tnz;
@@ -116,11 +122,6 @@ __global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
             // parts order them and the zero-length step between them can come out a
             // few ulps negative: clamped, or e^{-chi len} overflows in thick cells
             const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
-            if (it >= cap || (unsigned)ci >= (unsigned)P.nx || (unsigned)cj >= (unsigned)P.nz) {
-                capped = true;
-                break;
-            }
-            const Record<W> r = RecFmt<W, kStoreF32>::load(rp);
             const float nl2 = len * kNegLog2e;
             segments<W>(r.S, r.chi, nl2, I, T);
             if (COUNT) nseg += (th > th_prev);

@@ -34,6 +34,9 @@ struct StaticModel {
     static constexpr int kStride = RecFmt<W, ST>::kStride;
     static constexpr bool kPerBatch = true;
     static constexpr int kMinBlocks = 4;  // CTAs per SM the register budget targets
+    // record loaded at the top of each step: -3.3% (float32) on the 1024^2 benchmark
+    // solve; +5% with the bfloat16 / float16 unpacking (register pressure)
+    static constexpr bool kEarlyLoad = ST == kStoreF32;
     struct Params {
         int unused;
     };

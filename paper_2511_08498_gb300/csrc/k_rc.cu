@@ -71,7 +71,11 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
         rp = base + ((size_t)P.block_offset[blk] * P.chain + rc_level_offset(mip) + lz * side + lx) * REC;
     float th_prev = P.t_s, tl_prev = 0.0f;
 
+    Record<W> r;
     for (int it = 0;; ++it) {
+        // the current voxel's record is issued first: the stepping and crossing
+        // bookkeeping below hides its latency
+        if (mip >= 0) r = RecFmt<W, ST>::load(rp);
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
         float th = on_x ? tnx : tnz;
@@ -83,7 +87,6 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
         }
         const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
         const int cur_mip = mip;
-        const float* cur_rp = rp;
         if (!last) {
             if (it >= cap) { capped = true; break; }
             const float fv = (float)vox;
@@ -142,7 +145,6 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
             }
         }
         if (cur_mip >= 0) {
-            const Record<W> r = RecFmt<W, ST>::load(cur_rp);
             segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
             if (COUNT) nseg += (th > th_prev);
         }

@@ -25,6 +25,7 @@ struct VelModel {
     static constexpr int kStride = 4 + kNV * kRec;
     static constexpr bool kPerBatch = true;
     static constexpr int kMinBlocks = 4;
+    static constexpr bool kEarlyLoad = false;
     struct Params {
         int unused;
     };
