@@ -51,7 +51,7 @@ __global__ void k_pack_planes(long long n_cells, int n_lambda, int W, int n_batc
 }
 
 template <int W, bool COUNT>
-__global__ void __launch_bounds__(256) k_solve_dense(const DenseParams P)
+__global__ void __launch_bounds__(256, 4) k_solve_dense(const DenseParams P)
 {
     const int b = blockIdx.y;
     int i, j, p;

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256, 3) k_solve_dense3(const Dense3Params P)
                 capped = true;
                 break;
             }
-            const Record<W> r = RecFmt<W, kStoreF32>::template load<false>(rp);
+            const Record<W> r = RecFmt<W, kStoreF32>::load(rp);
             segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
             if (COUNT) nseg += (th > th_prev);
             if (th >= t2) break;

@@ -81,7 +81,13 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
     const float* rp = base + ((size_t)a0 * P.chain + level_offset3(mip) + (lz * side + ly) * side + lx) * REC;
     float th_prev = 0.0f, tl_prev = 0.0f;
 
+    Record<W> r;
     for (int it = 0;; ++it) {
+        // float32 records: issued at the top of the step (256-bit loads), so that the
+        // stepping and crossing bookkeeping hides their latency
+        if constexpr (ST == kStoreF32) {
+            if (mip >= 0) r = RecFmt<W, ST>::load(rp);
+        }
         const float tnx = Px * ax.ih, tny = Py * ay.ih, tnz = Pz * az.ih;
         const int axis = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
         const float th = axis == 0 ? tnx : (axis == 1 ? tny : tnz);
@@ -157,7 +163,7 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
             }
         }
         if (cur_mip >= 0) {
-            const Record<W> r = RecFmt<W, ST>::template load<false>(cur_rp);
+            if constexpr (ST != kStoreF32) r = RecFmt<W, ST>::template load<false>(cur_rp);
             segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
             if (COUNT) nseg += (th > th_prev);
         }
