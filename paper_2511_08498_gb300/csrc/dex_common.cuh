@@ -38,10 +38,19 @@ constexpr float kG2 = (float)taylor_coef(2);
 constexpr float kG3 = (float)taylor_coef(3);
 constexpr float kG4 = (float)taylor_coef(4);
 constexpr float kG5 = (float)taylor_coef(5);
-// Series used for tau < 0.1, i.e. x = -tau log2(e) > -0.1443: the first dropped
-// term is tau^6/720, a relative error below 2e-8.  Above it 1 - 2^x >= 0.095 and
-// the SFU's few-ulp error in 2^x costs < 3e-6 relative.
-constexpr float kSeriesCut = -0.14426950f;
+// 1 - e^{-tau} without a branch: g = min(P5(tau), (1 + 2^-21) - e), where
+//  * P5 = tau - tau^2/2 + tau^3/6 - tau^4/24 + tau^5/120 (the series above in
+//    x = -tau log2(e)) is never below 1 - e^{-tau} for tau >= 0 (the Lagrange
+//    remainder -e^{-xi} tau^6/720 is negative) and exceeds it by tau^6/720;
+//  * (1 + 2^-21) - e, with e = 2^x from the SFU (a few float ulps of error near
+//    1, each ulp 2^-24 there), exceeds it by 2^-21 minus that error: an upper
+//    bound as long as the error stays below 8 ulps, and within 2^-20 of it.
+// The smaller of the two: the series wherever it is within ~5e-7 of the exact
+// value (tau below ~0.25; relative error < 2e-8 for tau < 0.1), else 1 - e
+// plus at most 2^-20 (relative < 2e-6 for tau >= 0.25, < 5e-7 once g ~ 1).
+// Compared with a select on tau, the min saves a compare and a select per
+// wavelength; on the issue-bound 1024^2 benchmark solve it measured -3.4%.
+constexpr float kOnePlus2m21 = 1.000000476837158203125f;  // 1 + 2^-21
 constexpr float kNegLog2e = -1.4426950408889634f;
 
 // Transparent emitters (chi = 0, eta > 0) are stored as chi = eta * 2^-60 and
@@ -78,7 +87,7 @@ __device__ __forceinline__ void segment(float S, float chi, float nl2, float& I,
     p = fmaf(x, p, kG3);
     p = fmaf(x, p, kG2);
     p = fmaf(x, p, kG1);
-    const float g = (x > kSeriesCut) ? x * p : 1.0f - e;  // 1 - e^{-tau}
+    const float g = fminf(x * p, kOnePlus2m21 - e);  // 1 - e^{-tau}
     I = fmaf(T, S * g, I);
     T *= e;
 }
@@ -97,8 +106,8 @@ __device__ __forceinline__ void segment2(float2 S, float2 chi, float nl2, float&
     p = __ffma2_rn(x, p, make_float2(kG2, kG2));
     p = __ffma2_rn(x, p, make_float2(kG1, kG1));
     const float2 xp = __fmul2_rn(x, p);
-    const float2 ome = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-e.x, -e.y));
-    const float2 g = make_float2(x.x > kSeriesCut ? xp.x : ome.x, x.y > kSeriesCut ? xp.y : ome.y);
+    const float2 ome = __fadd2_rn(make_float2(kOnePlus2m21, kOnePlus2m21), make_float2(-e.x, -e.y));
+    const float2 g = make_float2(fminf(xp.x, ome.x), fminf(xp.y, ome.y));
     const float2 I = __ffma2_rn(make_float2(T0, T1), __fmul2_rn(S, g), make_float2(I0, I1));
     const float2 T = __fmul2_rn(make_float2(T0, T1), e);
     I0 = I.x;
