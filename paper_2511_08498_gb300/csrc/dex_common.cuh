@@ -44,10 +44,12 @@ constexpr float kG5 = (float)taylor_coef(5);
 //    remainder -e^{-xi} tau^6/720 is negative) and exceeds it by tau^6/720;
 //  * (1 + 2^-21) - e, with e = 2^x from the SFU (a few float ulps of error near
 //    1, each ulp 2^-24 there), exceeds it by 2^-21 minus that error: an upper
-//    bound as long as the error stays below 8 ulps, and within 2^-20 of it.
+//    bound while the error is below 2^-21 (8 such ulps), and within 2^-20 of it.
 // The smaller of the two: the series wherever it is within ~5e-7 of the exact
-// value (tau below ~0.25; relative error < 2e-8 for tau < 0.1), else 1 - e
-// plus at most 2^-20 (relative < 2e-6 for tau >= 0.25, < 5e-7 once g ~ 1).
+// value (tau below ~0.27; relative error < 3e-7 for tau < 0.1), else 1 - e
+// plus at most 2^-20.  Worst relative error, at the crossover near tau = 0.27:
+// 2.2e-6 with an exact 2^x, 3.8e-6 with 2^x off by 2^-21 (the float32 model of
+// this is tests/test_update_bound.py); < 5e-7 once g ~ 1.
 // Compared with a select on tau, the min saves a compare and a select per
 // wavelength; on the issue-bound 1024^2 benchmark solve it measured -3.4%.
 constexpr float kOnePlus2m21 = 1.000000476837158203125f;  // 1 + 2^-21
