@@ -80,7 +80,7 @@ def param_chain(P0, max_mip):
 
 
 def block_levels(chain, dv, c_kms, empty, block, lambda_batch, thr_eta, thr_chi, chi_ds_min=0.25,
-                 method="hum1wei24_cf", stats=False):
+                 method="hum1wei24", stats=False):
     """Per-batch block levels from the closest-to-core IoD test over the chain's children."""
     max_mip = len(chain) - 1
     passes, st = [], []
@@ -98,7 +98,7 @@ def block_levels(chain, dv, c_kms, empty, block, lambda_batch, thr_eta, thr_chi,
 
 
 def formal_solve(P_levels, level_map, block, lambda_batch, dv, c_kms, dirs, weights, probes, band=None,
-                 method="hum1wei24_cf", i_bc=0.0, want_intensity=False, profile=None):
+                 method="hum1wei24", i_bc=0.0, want_intensity=False, profile=None):
     """Accelerated CaV result (or the plain one with a single level and all-zero map).
 
     P_levels: parameter chain (list of [8][nz>>m][nx>>m]); level_map [n_batch][nbz][nbx].

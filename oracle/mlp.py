@@ -125,7 +125,7 @@ def weights_bf16(p):
     return q
 
 
-def profile_with_fallback(p, method="hum1wei24_cf"):
+def profile_with_fallback(p, method="hum1wei24"):
     """H(a, x, u) of the Core-and-Voigt solve with the surrogate: exp(network) inside
     the training domain (decided on float32 values, as the kernel does), the Voigt
     function of ``method`` at x - u outside it.  The network runs in float64 with

@@ -37,7 +37,7 @@ def _boxmax(a, f):
     return a.reshape(*lead, Z // f, f, X // f, f).max(axis=(-3, -1))
 
 
-def velocity_grids(P0, dv, c_kms, max_mip, n_vel=N_VEL, method="hum1wei24_cf"):
+def velocity_grids(P0, dv, c_kms, max_mip, n_vel=N_VEL, method="hum1wei24"):
     """Per level m: dict(V [nz>>m][nx>>m], vx, vz, eta [n_vel][L][...], chi [n_vel][L][...])."""
     es, cs, a, inv, vx, vz, ec, cc = P0
     speed = np.sqrt(vx * vx + vz * vz)
@@ -67,7 +67,7 @@ def _eta_chi_at(P, dv, vproj, c_kms, method):
     return cav_eta_chi(Pz, dv, 1.0, 0.0, c_kms, method=method)
 
 
-def rest_frame(P0, dv, c_kms, method="hum1wei24_cf"):
+def rest_frame(P0, dv, c_kms, method="hum1wei24"):
     return cav_eta_chi(P0, dv, 0.0, 0.0, c_kms, method=method)
 
 

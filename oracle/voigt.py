@@ -11,12 +11,10 @@ TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU-baseline leg).
         Z = (L + i z) / (L - i z),  p(Z) = sum_{n=1..N} a_n Z^(n-1),  L = sqrt(N / sqrt 2),
       where a_n are the Fourier coefficients of f(theta) = exp(-t^2) (L^2 + t^2),
       t = L tan(theta / 2), by the trapezoid rule on 2M = 4N points (f(-pi) = 0).
-* ``hum1wei24_cf``: the form the GPU evaluates: the same, except that for
-  5 <= |x| + y < 15 the Weideman sum is replaced by the 8-term Laplace continued
-  fraction w(z) = (i / sqrt(pi)) / (z - (1/2) / (z - 1 / (z - (3/2) / ...)))
-  (Gautschi 1970), evaluated from the innermost term.  In float32 the Weideman
-  sum cancels O(1) terms down to H ~ 1e-5 in the line wings; the continued
-  fraction does not.
+The GPU evaluates the same function H in float32 by its own scheme (its
+header states it); parity tests bound that scheme against ``exact`` and use
+``hum1wei24`` (the method's form, branch taken in float64) as the oracle of
+the moving-medium solves.
 """
 
 from __future__ import annotations
@@ -63,42 +61,10 @@ def hum1wei24(x, y):
     return out
 
 
-def laplace_cf(x, y, n_terms: int = 8):
-    """w(x + i y) from the Laplace continued fraction with ``n_terms`` levels."""
-    z = np.asarray(x, dtype=np.float64) + 1j * np.asarray(y, dtype=np.float64)
-    f = z.copy()
-    for k in range(n_terms, 0, -1):
-        f = z - (k / 2.0) / f
-    return 1j / (np.sqrt(np.pi) * f)
-
-
-def hum1wei24_cf(x, y):
-    """w(x + i y): Humlicek region I for s >= 15, continued fraction for 5 <= s < 15,
-    Weideman-24 for s < 5 (s = |x| + y).  The branch is chosen with s computed in
-    float32, the precision in which the GPU kernel takes the same decision; the
-    values are float64."""
-    x = np.asarray(x, dtype=np.float64)
-    y = np.asarray(y, dtype=np.float64)
-    x, y = np.broadcast_arrays(x, y)
-    s32 = np.abs(x).astype(np.float32) + y.astype(np.float32)
-    z = x + 1j * y
-    out = np.empty(x.shape, dtype=np.complex128)
-    far = s32 >= np.float32(15.0)
-    band = (s32 >= np.float32(5.0)) & ~far
-    near = ~(far | band)
-    with np.errstate(divide="ignore", invalid="ignore"):
-        out[far] = 1j * z[far] / (np.sqrt(np.pi) * (z[far] * z[far] - 0.5))
-    out[band] = laplace_cf(x[band], y[band])
-    out[near] = hum1wei24(x[near], y[near])   # s < 5 < 15: the Weideman branch
-    return out
-
-
 def voigt_h(a, x, method: str = "exact"):
     """H(a, x) = Re w(x + i a) (a >= 0)."""
     if method == "exact":
         return np.real(wofz(np.asarray(x, dtype=np.float64) + 1j * np.asarray(a, dtype=np.float64)))
     if method == "hum1wei24":
         return np.real(hum1wei24(x, a))
-    if method == "hum1wei24_cf":
-        return np.real(hum1wei24_cf(x, a))
     raise ValueError(method)
