@@ -1,12 +1,26 @@
 """Core-and-Voigt (moving medium) GPU path vs the float64 oracle.
 
 Tolerances, derived from the arithmetic:
-* Voigt function (float32, HUM1WEI24 with the continued-fraction band) vs the same
-  scheme in float64: relative 2e-5 where |x| + a < 2 or >= 5 (no cancellation),
-  and 1e-3 for 2 <= |x| + a < 5 with damping a >= 1e-3, where Weideman's sum cancels
-  O(1) terms down to H ~ 1e-5 (measured worst case 6.5e-4 at a = 1e-3).
-* CaV intensities vs the float64 oracle running the same scheme: eta and chi inherit
-  at most the Voigt function's relative error, so I and J are compared at 1e-3.
+* Voigt function.  The kernel's float32 scheme (region I for |x| + a >= 15, a
+  continued fraction below it down to 5, and for |x| + a < 5 the Taylor series
+  in a about the real axis, or Weideman's sum for a >= 0.25) against the
+  Faddeeva function: within 2e-5 relative for |x| + a < 15 (float32 emulation of
+  the scheme: 1.1e-5 worst, at a = 1e-3), and for |x| + a >= 15 within region
+  I's own truncation error (5.2e-5, pinned on the CPU) plus 2e-6 rounding.
+  Against the oracle's float64 HUM1WEI24 (the method's form): both share region
+  I, and below it HUM1WEI24 is within 3e-6 of the Faddeeva function (pinned), so
+  the two agree within 2e-5 + 3e-6 < 2.5e-5 -- except where |x| + a is within
+  float32 rounding of 15: the kernel decides the branch in float32, the oracle
+  in float64, and on that vanishing set they differ by region I's own error
+  (<= 5.2e-5).
+* CaV intensities.  eta and chi of a segment carry the profile's relative error
+  eps <= 2.5e-5 (5.4e-5 on the branch-edge set above; the continuum only dilutes
+  it) plus float32 rounding.  A ray's
+  intensity sum_i S_i (1 - e^{-tau_i}) prod_{j<i} e^{-tau_j} then moves by at
+  most eps (1 + tau_i e^{-tau_i} / (1 - e^{-tau_i}) + sum_{j<i} tau_j) relative
+  per term; the terms that matter sit at tau_{<i} of order one (deeper ones
+  carry the weight e^{-sum tau}, and sum tau e^{-sum tau} <= 1/e), so the bound
+  is a few eps: I and J are compared at 1e-4 (measured worst well below it).
 * Block levels: exact away from thresholds (checked on the oracle's side).
 """
 
@@ -35,18 +49,29 @@ def ctx():
 def test_voigt_kernel(ctx):
     from paper_2511_08498_gb300 import api
     x = np.concatenate([np.linspace(-40, 40, 40001), np.geomspace(40, 2000, 500)]).astype(np.float32)
-    for a in np.geomspace(1e-3, 1e-1, 5).astype(np.float32):
+    for a in np.concatenate([np.geomspace(1e-3, 1e-1, 5), [0.2, 0.26, 1.0, 3.0]]).astype(np.float32):
         A = np.full_like(x, a)
         h = api.voigt(ctx, torch.from_numpy(A).cuda(), torch.from_numpy(x).cuda()).cpu().numpy()
-        ref = voigt.voigt_h(A.astype(np.float64), x.astype(np.float64), method="hum1wei24_cf")
-        e = rel(h, ref)
-        s = np.abs(x) + a
-        assert e[(s < 2) | (s >= 5)].max() < 2e-5, (a, e[(s < 2) | (s >= 5)].max())
-        assert e.max() < 1e-3, (a, e.max())
-    # special values
+        a64, x64 = A.astype(np.float64), x.astype(np.float64)
+        exact = rel(h, voigt.voigt_h(a64, x64, method="exact"))
+        s = np.abs(x) + A   # the kernel picks its branch from |x| + a in float32
+        assert exact[s < 15].max() < 2e-5, (a, exact[s < 15].max())
+        assert exact[s >= 15].max() < 5.4e-5, (a, exact[s >= 15].max())
+        # against the float64 HUM1WEI24: 2.5e-5, except where |x| + a lies within float32
+        # rounding of 15 -- there the two take different sides of region I's boundary and
+        # differ by region I's own error (5.2e-5 at most, pinned on the CPU)
+        hum = rel(h, voigt.voigt_h(a64, x64, method="hum1wei24"))
+        edge = np.abs(np.abs(x64) + a64 - 15.0) <= 4.0 * np.spacing(np.float32(15.0))
+        assert hum[~edge].max() < 2.5e-5, (a, hum[~edge].max())
+        assert hum[edge].max(initial=0.0) < 5.4e-5
+    # special values: H(0, x) = e^{-x^2}, H(a, 0) = e^{a^2} erfc(a)
+    from scipy.special import erfcx
     z = torch.zeros(3, device="cuda")
     h0 = api.voigt(ctx, z, torch.tensor([0.0, 1.0, 2.0], device="cuda")).cpu().numpy()
     np.testing.assert_allclose(h0, np.exp(-np.array([0.0, 1.0, 4.0])), rtol=2e-5)
+    av = np.array([1e-3, 0.1, 0.3, 2.0], np.float32)
+    hc = api.voigt(ctx, torch.from_numpy(av).cuda(), torch.zeros(4, device="cuda")).cpu().numpy()
+    np.testing.assert_allclose(hc, erfcx(av.astype(np.float64)), rtol=2e-5)
 
 
 def model(nx=128, nz=96, n_lambda=16, seed=600):
@@ -65,7 +90,7 @@ def gpu_cav(ctx, m, W, max_mip, iod, dirs, w, band=None, cm=0.25, mlp_params=Non
     return grid, mp, J, I, seg
 
 
-def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei24_cf", stats=False, profile=None):
+def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei24", stats=False, profile=None):
     P0 = cav.param_arrays(m)
     chain = cav.param_chain(P0, max_mip)
     empty = omips.block_empty(np.stack([m["eta_star"], m["eta_c"]]), np.stack([m["chi_star"], m["chi_c"]]), 16)
@@ -94,8 +119,8 @@ def test_cav_solve_matches_oracle(ctx, max_mip, iod, band):
     p = o["probes"]
     eI = rel(I.cpu().numpy()[:, :, p], o["I"])
     eJ = rel(J.cpu().numpy()[:, p], o["J"])
-    assert eI.max() < 1e-3, f"I max rel err {eI.max():.3e}"
-    assert eJ.max() < 1e-3, f"J max rel err {eJ.max():.3e}"
+    assert eI.max() < 1e-4, f"I max rel err {eI.max():.3e}"
+    assert eJ.max() < 1e-4, f"J max rel err {eJ.max():.3e}"
 
 
 def test_cav_static_limit_is_the_static_line(ctx):
@@ -110,7 +135,7 @@ def test_cav_static_limit_is_the_static_line(ctx):
     dirs, w = synth.directions(8)
     _, _, J, _, _ = gpu_cav(ctx, m, 8, 0, 1.0, dirs, w)
     o = oracle_cav(m, 8, 0, 1.0, dirs, w, method="exact")
-    assert rel(J.cpu().numpy()[:, o["probes"]], o["J"]).max() < 1e-3
+    assert rel(J.cpu().numpy()[:, o["probes"]], o["J"]).max() < 1e-4
 
 
 @pytest.mark.parametrize("max_mip,band", [(0, None), (2, [4.5, 12.0])])
@@ -118,7 +143,7 @@ def test_cav_with_surrogate_profile_matches_oracle(ctx, max_mip, band):
     """The Core-and-Voigt solve with the learned profile (dex_formal_solve_cav_mlp):
     the network inside its training domain, HUM1WEI24 outside it, against the
     oracle doing the same in float64.  The network's float32 evaluation adds
-    ~1e-6 relative to ln H; the fallback carries the Voigt tolerance (1e-3)."""
+    ~1e-6 relative to ln H; the fallback carries the Voigt bound (module docstring)."""
     from oracle import mlp as omlp
     m = model(nx=64, nz=48, n_lambda=8, seed=620)
     p = synth.mlp.initial_params(synth.SEED_BASE + 621, scale=0.5)
@@ -126,8 +151,8 @@ def test_cav_with_surrogate_profile_matches_oracle(ctx, max_mip, band):
     _, _, J, I, _ = gpu_cav(ctx, m, 8, max_mip, 1.0, dirs, w, band=band, mlp_params=p)
     o = oracle_cav(m, 8, max_mip, 1.0, dirs, w, band=band, profile=omlp.profile_with_fallback(p))
     pr = o["probes"]
-    assert rel(I.cpu().numpy()[:, :, pr], o["I"]).max() < 1e-3
-    assert rel(J.cpu().numpy()[:, pr], o["J"]).max() < 1e-3
+    assert rel(I.cpu().numpy()[:, :, pr], o["I"]).max() < 1e-4
+    assert rel(J.cpu().numpy()[:, pr], o["J"]).max() < 1e-4
     # and the network did replace the profile: the result differs from exact CaV
     _, _, Jx, _, _ = gpu_cav(ctx, m, 8, max_mip, 1.0, dirs, w, band=band)
     assert rel(J.cpu().numpy()[:, pr], Jx.cpu().numpy()[:, pr]).max() > 1e-2

@@ -118,8 +118,10 @@ def test_targets_match_oracle_voigt(ctx):
     y = api.mlp_targets(ctx, dev(xau)).cpu().numpy().astype(np.float64)
     ctx.check()
     x32 = (xau[:, 0] - xau[:, 2]).astype(np.float64)  # the kernel forms x - u in float32
-    ref = np.log(ovoigt.voigt_h(xau[:, 1].astype(np.float64), x32, method="hum1wei24_cf"))
-    assert np.abs(y - ref).max() < 1e-3
+    ref = np.log(ovoigt.voigt_h(xau[:, 1].astype(np.float64), x32, method="hum1wei24"))
+    # the kernel's float32 Voigt is within 2e-5 relative of the float64 HUM1WEI24
+    # (tests/test_cav_parity.py::test_voigt_kernel); ln H then differs by <= 2e-5 + rounding
+    assert np.abs(y - ref).max() < 3e-5
     assert np.median(np.abs(y - ref)) < 2e-6
 
 

@@ -1,9 +1,10 @@
 """Velocity interpolation (Section 3.1) on the GPU vs the float64 oracle.
 
-The grid values come from the float32 Voigt function (see test_cav_parity for its
-conditioning bound, 1e-3 relative); interpolation and traversal add only float32
-rounding, so intensities are compared at 1e-3.  Block levels (rest-frame IoD)
-must agree exactly.
+The grid values come from the float32 Voigt function, within 2.5e-5 relative of
+the oracle's float64 HUM1WEI24 (test_cav_parity derives the bound and the 1e-4
+tolerance it implies for intensities); interpolation and traversal add only
+float32 rounding, so intensities are compared at 1e-4.  Block levels
+(rest-frame IoD) must agree exactly.
 """
 
 import numpy as np
@@ -46,5 +47,5 @@ def test_velinterp_matches_oracle(ctx, max_mip, iod, band):
     grids = ov.velocity_grids(P0, m["dv"], m["c_kms"], max_mip)
     probes = omips.probes_of_blocks(empty, 16)
     Jr, Ir = ov.formal_solve(grids, lev, 16, 8, dirs, w, probes, band=band, want_intensity=True)
-    assert rel(I.cpu().numpy()[:, :, probes], Ir).max() < 1e-3
-    assert rel(J.cpu().numpy()[:, probes], Jr).max() < 1e-3
+    assert rel(I.cpu().numpy()[:, :, probes], Ir).max() < 1e-4
+    assert rel(J.cpu().numpy()[:, probes], Jr).max() < 1e-4
