@@ -59,3 +59,37 @@ def robust_level_mask3(stats, level_map, lambda_batch, max_mip, te, tc, cm, eps=
             good = good and rf[L_][idx]
         ok[idx] = good
     return ok
+
+
+def candidate_levels(stats, level_map, lambda_batch, block, max_mip, te, tc, cm, eps=1e-4):
+    """Every level a block-batch may take when its decisions near a threshold go
+    either way: {index: [levels]} for the block-batches that are not robust.
+
+    Level l is a candidate when no decision of levels 1..l fails robustly (each
+    level's groups can all pass) and, below max_mip, level l + 1 does not pass
+    robustly (it can fail)."""
+    n_batch, nbz, nbx = level_map.shape
+    rp, rf = [], []
+    for st in stats:
+        L = st["iod_eta"].shape[0]
+        with np.errstate(invalid="ignore"):
+            p = ((st["iod_eta"] < te * (1 - eps)) & (st["iod_chi"] < tc * (1 - eps))) | (st["chi_ds"] < cm * (1 - eps))
+            f = ((st["iod_eta"] > te * (1 + eps)) | (st["iod_chi"] > tc * (1 + eps))) & (st["chi_ds"] > cm * (1 + eps))
+        side = p.shape[1] // nbz
+
+        def per_batch(a, red):
+            blk = red(a.reshape(L, nbz, side, nbx, side), axis=(2, 4))
+            return np.stack([red(blk[b * lambda_batch:(b + 1) * lambda_batch], axis=0) for b in range(n_batch)])
+        rp.append(per_batch(p, np.all))
+        rf.append(per_batch(f, np.any))
+    robust = robust_level_mask(stats, level_map, lambda_batch, block, max_mip, te, tc, cm, eps)
+    out = {}
+    for idx in zip(*np.nonzero(~robust)):
+        cands = []
+        for lv in range(max_mip + 1):
+            can_pass = all(not rf[m - 1][idx] for m in range(1, lv + 1))
+            can_stop = lv == max_mip or not rp[lv][idx]
+            if can_pass and can_stop:
+                cands.append(lv)
+        out[tuple(int(v) for v in idx)] = cands
+    return out
