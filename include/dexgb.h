@@ -72,6 +72,25 @@ int dex_ctx_destroy(dex_ctx* ctx);
 int dex_ctx_set_stream(dex_ctx* ctx, void* stream);
 
 /*
+ * Traversal of the static accelerated solve (dex_formal_solve_hdda) for W = 8:
+ *   DEX_TRAVERSAL_PER_BATCH (default): one walk per ray and wavelength batch.
+ *   DEX_TRAVERSAL_SHARED: one walk per ray for two wavelength batches, b and
+ *     n_batch - 1 - b.  In every block the walk steps through the voxels of the
+ *     finer of the two batches' levels there, and each batch integrates its own
+ *     voxel (at its own level, Section 4.1) when the walk leaves it, over the
+ *     length between the same two planes its own walk would use: J, I and the
+ *     executed segment count equal those of the per-batch walk.  Needs at least
+ *     two batches and grids of at most 24576 blocks (the CTA stages one 32-bit
+ *     word per block); otherwise the per-batch walk runs.  On a GB300 it is the
+ *     slower of the two on the static-line workload (its larger per-thread
+ *     state halves the resident warps).
+ * Any other mode -> DEX_ERR_ARG.  The setting belongs to the context.
+ */
+#define DEX_TRAVERSAL_PER_BATCH 0
+#define DEX_TRAVERSAL_SHARED 1
+int dex_ctx_set_traversal(dex_ctx* ctx, int mode);
+
+/*
  * Synchronise the context's stream, read and clear the device status word.
  * Returns DEX_OK or the OR of the device error bits (DEX_ERR_TRAVERSAL_CAP,
  * DEX_ERR_NUMERIC), or DEX_ERR_CUDA if the stream reported a CUDA error.
@@ -472,11 +491,16 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
  * loads the library until the process exits.  The caller still provides all
  * inputs and outputs (descriptors, J, optional done_ns / start_ns).
  *
- * - It calls no cudaMalloc/cudaFree and makes no other allocation, on the device
- *   or the host; the counter is reset by the call before the launch.
- * - The first call on a device looks up the device address of the array (with
- *   that device current) and caches it; make that first call before any stream
- *   capture.
+ * - It calls no cudaMalloc/cudaFree and no other allocating routine, on the
+ *   device or the host; the counter is reset by the call before the launch.
+ *   The CUDA driver itself reserves device memory when it first loads the
+ *   library's kernels into a context (code and static data, this array
+ *   included), and it may do that lazily on the first call of any dex_* entry
+ *   point on the device: a caller that must not see that happen during its solve
+ *   makes one call at initialisation, before any stream capture.
+ * - Every call looks up the array's device address on the current device (a
+ *   runtime table look-up, not an allocation), so a cudaDeviceReset between
+ *   calls is safe: the next call uses the new context's array.
  * - Every call shares the same array: calls that overlap on the GPU (different
  *   streams, or different contexts on one device) race on the counter.
  *   Serialise them.

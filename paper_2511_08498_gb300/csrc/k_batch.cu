@@ -8,7 +8,6 @@
 // staged block states and quadrature are reused, and the L2 working set stays
 // one atmosphere batch wide.  Per-atmosphere completion times (globaltimer, ns)
 // are recorded when requested.
-#include <mutex>
 
 #include "hdda.cuh"
 
@@ -132,25 +131,17 @@ __global__ void __launch_bounds__(256) k_batch_solve(const BatchParams P)
 
 }  // namespace
 
-// Device address of the static scratch array on the current device, looked up
-// once per device (with that device current) and cached.  The array's host-side
-// name is not a device address, so kernels must be given this pointer.
+// Device address of the static scratch array on the current device.  The array's
+// host-side name is not a device address, so kernels must be given this pointer.
+// It is looked up on every call (a runtime table look-up, no allocation) rather
+// than cached: after a cudaDeviceReset the device's context, and with it the
+// array, is a new one, and a cached address would point into the old context.
 cudaError_t noalloc_scratch(unsigned int** out)
 {
-    static std::mutex mu;
-    static unsigned int* ptr[256] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (ptr[dev] == nullptr) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        ptr[dev] = static_cast<unsigned int*>(p);
-    }
-    *out = ptr[dev];
+    *out = static_cast<unsigned int*>(p);
     return cudaSuccess;
 }
 

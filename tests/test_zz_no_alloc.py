@@ -8,6 +8,8 @@ array.  This test calls that entry point through the C ABI twice in a row (the
 second call reuses the array the first one left behind) and checks both results
 against the ordinary dex_batch_solve, which takes its counter from the caller.
 The two run the same kernel in the same order, so the results must be identical.
+Around the second call it also checks that the device's free memory
+(cudaMemGetInfo) and torch's allocation count do not change.
 
 Collected last on purpose: if it fails, a run that stops at the first failure has
 already run every other test.
@@ -56,8 +58,15 @@ def test_noalloc_batch_matches_batch_solve_twice():
     for call in range(2):                                # the second call reuses the static scratch
         for a in atms:
             a["J"].fill_(-1.0)
+        torch.cuda.synchronize()
+        # after the first call (which may make the driver load the library's kernels)
+        # the call must change neither the device's free memory nor torch's allocations
+        free0, n_alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_stats().get("allocation.all.allocated", 0)
         api.batch_solve_noalloc(ctx, items, 8, done_ns=done, start_ns=start)
         ctx.check()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0, "device free memory changed during the call"
+            assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == n_alloc0
         for a, r in zip(atms, ref):
             assert torch.equal(a["J"], r), f"call {call}: result differs from dex_batch_solve"
         assert (done.cpu().numpy() >= int(start.item())).all()
