@@ -49,11 +49,16 @@ BAND = [6.0, 24.0, 96.0]
 WORKLOAD = (f"sparse static-line atmosphere {NX}x{NZ}, 16^2 blocks, 40% empty, {N_LAMBDA} wavelengths, "
             f"{N_DIR} directions, VLM mip 0-{MAX_MIP}, IoD threshold {THR:g}, level distance limits "
             f"{BAND}, HDDA, FP32")
-# accelerated variants reported beside the timed step:
-# (name, IoD threshold, distance limits, brick storage 0 float32 / 1 bfloat16 / 2 float16)
-VARIANTS = [("strict_iod_1e-3", THR_STRICT, BAND, 0), ("paper_iod_1", 1.0, BAND, 0),
-            ("unlimited_vlm", 1e30, BAND, 0), ("no_distance_limit_iod_1e-2", THR, None, 0),
-            ("bf16_bricks", THR, BAND, 1), ("f16_bricks", THR, BAND, 2)]
+# accelerated variants reported beside the timed step: (name, IoD threshold, distance
+# limits, brick storage 0 float32 / 1 bfloat16 / 2 float16, one walk shared by two
+# wavelength batches (True) or one walk per batch (False))
+VARIANTS = [("strict_iod_1e-3", THR_STRICT, BAND, 0, False), ("paper_iod_1", 1.0, BAND, 0, False),
+            ("unlimited_vlm", 1e30, BAND, 0, False), ("no_distance_limit_iod_1e-2", THR, None, 0, False),
+            ("bf16_bricks", THR, BAND, 1, False), ("f16_bricks", THR, BAND, 2, False),
+            ("shared_walk_iod_1e-2", THR, BAND, 0, True), ("shared_walk_unlimited_vlm", 1e30, BAND, 0, True)]
+# the bar a variant must meet to be quoted as the fastest acceptable one: J error
+# p99.9 <= 0.5% against the plain solve (the population error is checked separately)
+ERR_BAR_PCT = 0.5
 # Each segment-wavelength update needs one 2^x on the special-function units, so
 # their measured 2^x throughput (dex_measure_ex2_rate, ~30 per SM per clock on a
 # GB300 at 2070 MHz) bounds the updates per second of the solve kernels.
@@ -177,8 +182,9 @@ class Workload:
         self.api.synth_static_line(self.ctx, d["chi_c"], d["s_c"], d["s_l"], d["ratio"], d["dld"], d["dlam"],
                                    eta=self.eta, chi=self.chi)
 
-    def step(self, thr=THR, band=BAND, ev=None, count=False, storage=0):
+    def step(self, thr=THR, band=BAND, ev=None, count=False, storage=0, shared=False):
         api = self.api
+        self.ctx.set_traversal(shared)
         self.synth()
         self.grid = api.grid_build(self.ctx, NX, NZ, self.eta, self.chi, out=self.grid)
         self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, W, MAX_MIP, thr, thr, CHI_DS_MIN,
@@ -207,7 +213,8 @@ class Workload:
 # ncu summary of the HDDA kernel's DRAM traffic on this workload, and the sources
 # whose hash it records: the figure is reported only while they are unchanged
 TRAFFIC_PROFILE = os.path.join("profiles", "k_solve_hdda_static_w8_1024_dram.md")
-HDDA_SOURCES = [os.path.join("paper_2511_08498_gb300", "csrc", f) for f in ("hdda.cuh", "k_hdda.cu", "dex_common.cuh")]
+HDDA_SOURCES = [os.path.join("paper_2511_08498_gb300", "csrc", f)
+                for f in ("hdda.cuh", "k_hdda.cu", "k_hdda_mb.cu", "dex_common.cuh")]
 # ... and, from the internal header, the kernel's parameter structs
 HDDA_STRUCTS = (os.path.join("paper_2511_08498_gb300", "csrc", "dex_internal.h"), ("HddaParams",))
 
@@ -346,13 +353,14 @@ def native(args):
 
     # accelerated variants, same protocol
     variants = {}
-    for name, thr, band, storage in VARIANTS:
-        seg_v = wl.step(thr=thr, band=band, count=True, storage=storage)
+    for name, thr, band, storage, shared in VARIANTS:
+        seg_v = wl.step(thr=thr, band=band, count=True, storage=storage, shared=shared)
         J_v = wl.J[:, probes.long()].double()
-        vt, vk = time_steps(lambda ev: wl.step(thr=thr, band=band, ev=ev, storage=storage),
+        vt, vk = time_steps(lambda ev: wl.step(thr=thr, band=band, ev=ev, storage=storage, shared=shared),
                             max(2, min(args.steps, 3)), 1, torch, flush)
         v_s = sum(vt) / 1e3 / len(vt)
         variants[name] = {"iod_threshold": thr, "distance_limits": band, "storage": ["f32", "bf16", "f16"][storage],
+                          "walk": "shared by wavelength batches b, n-1-b" if shared else "one per wavelength batch",
                           "ms_per_step": v_s * 1e3, "hdda_ms": sum(vk) / len(vk),
                           "value": dense_seg_lambda / v_s, "speedup_vs_plain": plain_s / v_s,
                           "executed_fraction": int(seg_v.item()) * W / dense_seg_lambda,
@@ -407,7 +415,7 @@ def native(args):
                    "l2": "flushed between steps (256 MiB write); inputs and bricks also exceed L2",
                    "timing": "CUDA events per step on the launch stream, flush outside the events",
                    "parallelism": "one independent atmosphere per rank (weak scaling, no collective)"},
-        "roofline": {"bound": "alu", "kernel": "k_solve_hdda<8>", "achieved": achieved, "peak": sfu_peak,
+        "roofline": {"bound": "alu", "kernel": "k_solve_hdda_t<8> (one walk per wavelength batch)", "achieved": achieved, "peak": sfu_peak,
                      "unit": "G seg-lambda updates/s", "frac": achieved / sfu_peak,
                      "traffic": measured_traffic(), "traffic_unit": "DRAM bytes per launch (ncu, one capture)",
                      "peak_basis": "measured 2^x throughput of the special-function units "
@@ -435,6 +443,15 @@ def native(args):
         "gpu_launches": wl.launches_per_step * args.steps,
         "clocks": clk.summary(),
     }
+    # the fastest accelerated configuration whose J error meets the bar
+    cands = [("timed_step_iod_1e-2", out["speedup_vs_plain"], out["j_err_pct_vs_plain"]["p99.9"])]
+    cands += [(n, v["speedup_vs_plain"], v["j_err_pct_vs_plain"]["p99.9"]) for n, v in variants.items()]
+    within = [c for c in cands if c[2] <= ERR_BAR_PCT]
+    if within:
+        best = max(within, key=lambda c: c[1])
+        out["fastest_within_bar"] = {"variant": best[0], "speedup_vs_plain": best[1], "j_err_pct_p99.9": best[2],
+                                     "bar": f"J error p99.9 <= {ERR_BAR_PCT}% vs the plain solve"}
+    ctx.set_traversal(False)
     out["cascades"] = cascade_check(ctx, wl, torch, flush)
     if not args.no_populations and args.phase == "all":
         out["populations"] = population_check(ctx, torch)

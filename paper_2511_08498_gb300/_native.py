@@ -26,6 +26,7 @@ PROTOTYPES = {
     "dex_ctx_create": (c_int, [c_int, c_void_p, ctypes.POINTER(c_void_p)]),
     "dex_ctx_destroy": (c_int, [c_void_p]),
     "dex_ctx_set_stream": (c_int, [c_void_p, c_void_p]),
+    "dex_ctx_set_traversal": (c_int, [c_void_p, c_int]),
     "dex_ctx_check": (c_int, [c_void_p]),
     "dex_last_error": (c_char_p, [c_void_p]),
     "dex_planes_floats": (c_size_t, [c_int, c_int, c_int]),

@@ -52,6 +52,11 @@ class Context:
         self.stream = stream
         self._rc(lib().dex_ctx_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
 
+    def set_traversal(self, shared: bool):
+        """Static accelerated solve at W = 8: one walk per ray and wavelength
+        batch (``shared=False``, the default) or one walk for two batches."""
+        self._rc(lib().dex_ctx_set_traversal(self.handle, 1 if shared else 0))
+
     def _rc(self, rc: int):
         if rc != 0:
             msg = lib().dex_last_error(self.handle)

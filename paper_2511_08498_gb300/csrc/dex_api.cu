@@ -12,6 +12,7 @@ struct dex_ctx {
     int device;
     cudaStream_t stream;
     unsigned int* status;  // device word, OR of DEX_ERR_* bits raised by kernels
+    int traversal = DEX_TRAVERSAL_PER_BATCH;  // static accelerated solve: one walk per wavelength batch
     char msg[512];
 };
 
@@ -198,6 +199,15 @@ int dex_ctx_destroy(dex_ctx* ctx)
     cudaFree(ctx->status);
     delete ctx;
     return DEX_OK;
+}
+
+int dex_ctx_set_traversal(dex_ctx* ctx, int mode)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (mode != DEX_TRAVERSAL_PER_BATCH && mode != DEX_TRAVERSAL_SHARED)
+        return fail(ctx, DEX_ERR_ARG, "traversal mode must be DEX_TRAVERSAL_PER_BATCH or DEX_TRAVERSAL_SHARED");
+    ctx->traversal = mode;
+    return ok(ctx);
 }
 
 int dex_ctx_set_stream(dex_ctx* ctx, void* stream)
@@ -428,6 +438,7 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     dex::HddaParams P{};
     P.storage = storage;
     P.n_band = -1;
+    P.traversal = kind == 0 ? ctx->traversal : DEX_TRAVERSAL_PER_BATCH;
     if (band != nullptr && n_band >= 0) {
         if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);
         for (int q = 0; q < n_band; ++q) {

@@ -40,6 +40,7 @@ struct MipParams {
 struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
+    int traversal;   // DEX_TRAVERSAL_PER_BATCH or DEX_TRAVERSAL_SHARED (static model, W = 8)
     float band[4];
     long long n_cells;
     const float* bricks;
@@ -187,6 +188,9 @@ cudaError_t launch_grid_build(cudaStream_t s, int nx, int nz, int n_lambda, cons
                               int* block_offset, int* active, int* n_active);
 cudaError_t launch_mips_build(cudaStream_t s, const MipParams& p);
 cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& p);
+// one traversal per ray for up to four wavelength batches (k_hdda_mb.cu)
+bool solve_hdda_shared_applies(const HddaParams& p);
+cudaError_t launch_solve_hdda_shared(cudaStream_t s, const HddaParams& p);
 
 // --------------------------------------------------- radiance cascades --
 struct RcParams {

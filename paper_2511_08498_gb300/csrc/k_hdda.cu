@@ -65,6 +65,7 @@ cudaError_t launch_hdda_kernel(K kernel, dim3 grid, size_t smem, cudaStream_t s,
 cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& P)
 {
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
+    if (solve_hdda_shared_applies(P)) return launch_solve_hdda_shared(s, P);
     // W = 8 on grids of at most kInfoMaxBlocks blocks: one shared-memory word per
     // block (InfoLookup); otherwise the packed state words (WordLookup)
     const long long n_blocks = (long long)P.nbx * P.nbz;
