@@ -86,6 +86,19 @@ int dex_ctx_set_stream(dex_ctx* ctx, void* stream);
  *     state halves the resident warps).
  * Any other mode -> DEX_ERR_ARG.  The setting belongs to the context.
  */
+/*
+ * Own-cell emission in the formal solutions (context setting, default 1 =
+ * included).  With include = 0, dex_formal_solve_dense and dex_formal_solve_hdda
+ * leave out the emission of each probe's own cell (the first segment of every
+ * ray; for the accelerated solve the probe's own voxel, which is its MIP-0 cell
+ * wherever the distance limits keep the probe's block at level 0): I and J then
+ * hold the radiation arriving from beyond the cell, attenuated by it (Jext, the
+ * input of dex_mali_rates).  The accelerated solve supports it for W = 8 and
+ * float32 bricks; every other solver returns DEX_ERR_UNSUPPORTED while it is
+ * off.  include not 0 or 1 -> DEX_ERR_ARG.
+ */
+int dex_ctx_set_own_cell(dex_ctx* ctx, int include);
+
 #define DEX_TRAVERSAL_PER_BATCH 0
 #define DEX_TRAVERSAL_SHARED 1
 int dex_ctx_set_traversal(dex_ctx* ctx, int mode);
@@ -326,6 +339,54 @@ int dex_rates_accumulate(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_
  */
 int dex_se_solve(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature, const float* ne,
                  const float* nh, const double* jbar, double* pops);
+
+/*
+ * MALI (Section 4.1: multilevel accelerated lambda iteration with same-transition
+ * preconditioning and a diagonal approximate operator, after Rybicki & Hummer
+ * 1992).  One iteration from populations n' (pops) and the J of their emissivity
+ * and opacity (the formal solution of dex_atom_eta_chi's output):
+ *
+ *   dex_mali_rates       per line and cell, in float64,
+ *                          rho      = 1 - Psibar,
+ *                          Psibar   = sum_k w_k phi_k Lambda*_k chi_line,k / chi_k,
+ *                          Jbar_eff = sum_k w_k phi_k (J_k - Lambda*_k eta_line,k / chi_k),
+ *                        over the line's samples (trapezoid weights in frequency,
+ *                        the renormalised profile of dex_rates_accumulate), with
+ *                        eta, chi of n' (float64, per cell) and the diagonal
+ *                        operator of the long-characteristics solve
+ *                          Lambda*_k = sum_d w_d (1 - e^{-chi_k l_d}),
+ *                          l_d = 1 / (2 max(|d_x|, |d_z|)) cells
+ *                        (the path from the probe's centre to its cell boundary;
+ *                        the own cell adds S (1 - e^{-chi l_d}) to I_d).  The
+ *                        input Jext is the formal solution with each probe's
+ *                        own-cell emission left out (dex_ctx_set_own_cell(ctx, 0)),
+ *                        J = Jext + Lambda* (eta_line + eta_c) / chi, and the call
+ *                        evaluates Jbar_eff = sum_k w_k phi_k (Jext_k + Lambda*_k
+ *                        eta_c,k / chi_k) and rho = sum_k w_k phi_k ((1 - Lambda*_k)
+ *                        chi_line,k + chi_c) / chi_k (the profile has unit
+ *                        quadrature): the same numbers, without the cancellations
+ *                        of J minus the own-cell term and of 1 minus Psibar, which
+ *                        in cells thick at every sampled frequency exceed float32.
+ *                        dirs, weights: host [n_dir][2], [n_dir] as in the
+ *                        solvers.  rho, jeff: float64 device [n_line][n_cells].
+ *   dex_se_solve_preconditioned
+ *                        the statistical equilibrium of dex_se_solve with the
+ *                        preconditioned radiative rates R_ul = A_ul rho + B_ul
+ *                        Jbar_eff, R_lu = B_lu Jbar_eff: the MALI populations.
+ *   dex_max_rel_change   out (device, one double) = max over cells with T > 0 and
+ *                        over levels of |new - old| / new (the convergence
+ *                        measure of Section 4.1); a non-finite value propagates.
+ *
+ * Arguments as dex_rates_accumulate / dex_se_solve; null buffers or bad sizes ->
+ * DEX_ERR_ARG.  The caller owns every buffer.
+ */
+int dex_mali_rates(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_lambda, const double* lambda_nm,
+                   const int* line_tag, const float* temperature, const float* ne, const double* pops,
+                   const float* Jext, int n_dir, const float* dirs, const float* weights, double* rho, double* jeff);
+int dex_se_solve_preconditioned(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature,
+                                const float* ne, const float* nh, const double* rho, const double* jeff, double* pops);
+int dex_max_rel_change(dex_ctx* ctx, int n_level, int n_cells, const float* temperature, const double* old_pops,
+                       const double* new_pops, double* out);
 
 /* ------------------------------------------------------------------ Voigt --
  *

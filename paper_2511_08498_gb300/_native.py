@@ -27,6 +27,7 @@ PROTOTYPES = {
     "dex_ctx_destroy": (c_int, [c_void_p]),
     "dex_ctx_set_stream": (c_int, [c_void_p, c_void_p]),
     "dex_ctx_set_traversal": (c_int, [c_void_p, c_int]),
+    "dex_ctx_set_own_cell": (c_int, [c_void_p, c_int]),
     "dex_ctx_check": (c_int, [c_void_p]),
     "dex_last_error": (c_char_p, [c_void_p]),
     "dex_planes_floats": (c_size_t, [c_int, c_int, c_int]),
@@ -48,6 +49,10 @@ PROTOTYPES = {
     "dex_rates_accumulate": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p]),
     "dex_se_solve": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 5),
+    "dex_mali_rates": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p] + [c_void_p] * 4 +
+                       [c_int, c_fp, c_fp, c_void_p, c_void_p]),
+    "dex_se_solve_preconditioned": (c_int, [c_void_p, c_void_p, c_int] + [c_void_p] * 6),
+    "dex_max_rel_change": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dex_voigt": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "dex_cav_grid_build": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dex_cav_brick_floats": (c_size_t, [c_int, c_int]),

@@ -57,6 +57,11 @@ class Context:
         batch (``shared=False``, the default) or one walk for two batches."""
         self._rc(lib().dex_ctx_set_traversal(self.handle, 1 if shared else 0))
 
+    def set_own_cell(self, include: bool):
+        """Include (default) or leave out each probe's own-cell emission in the
+        plain and accelerated solves (``dex_ctx_set_own_cell``)."""
+        self._rc(lib().dex_ctx_set_own_cell(self.handle, 1 if include else 0))
+
     def _rc(self, rc: int):
         if rc != 0:
             msg = lib().dex_last_error(self.handle)
@@ -395,6 +400,95 @@ def lambda_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, 
         jbar = rates_accumulate(ctx, atom, lam_nm, tag, T, J, out=jbar)
         pops = se_solve(ctx, atom, T, ne, nh, jbar, out=pops)
     return pops
+
+
+def mali_rates(ctx: Context, atom: Atom, lam_nm, tag, T, ne, pops, Jext, dirs, weights, rho=None, jeff=None):
+    """``dex_mali_rates``: (rho = 1 - Psibar, Jbar_eff) per line and cell, float64,
+    from the populations and the formal solution without the own-cell emission."""
+    n = T.numel()
+    lam, tg, lp, tp = _lam_arrays(lam_nm, tag)
+    d, w = _quadrature(dirs, weights)
+    shape = (max(atom.n_line, 1), n)
+    rho = torch.empty(shape, dtype=torch.float64, device=T.device) if rho is None else rho
+    jeff = torch.empty(shape, dtype=torch.float64, device=T.device) if jeff is None else jeff
+    fp = ctypes.POINTER(ctypes.c_float)
+    ctx._rc(lib().dex_mali_rates(ctx.handle, ctypes.byref(atom), n, lam.size, lp, tp, _ptr(T), _ptr(ne), _ptr(pops),
+                                 _ptr(Jext), d.shape[0], d.ctypes.data_as(fp), w.ctypes.data_as(fp), _ptr(rho),
+                                 _ptr(jeff)))
+    return rho, jeff
+
+
+def se_solve_preconditioned(ctx: Context, atom: Atom, T, ne, nh, rho, jeff, out=None):
+    """``dex_se_solve_preconditioned``: the MALI populations from the preconditioned rates."""
+    n = T.numel()
+    if out is None:
+        out = torch.empty((atom.n_level, n), dtype=torch.float64, device=T.device)
+    ctx._rc(lib().dex_se_solve_preconditioned(ctx.handle, ctypes.byref(atom), n, _ptr(T), _ptr(ne), _ptr(nh),
+                                              _ptr(rho), _ptr(jeff), _ptr(out)))
+    return out
+
+
+def max_rel_change(ctx: Context, T, old, new, out=None):
+    """``dex_max_rel_change`` into a 1-element float64 device tensor."""
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=T.device)
+    ctx._rc(lib().dex_max_rel_change(ctx.handle, int(old.shape[0]), T.numel(), _ptr(T), _ptr(old), _ptr(new),
+                                     _ptr(out)))
+    return out
+
+
+def mali_iteration(ctx: Context, atom: Atom, lam_nm, tag, T, ne, nh, nx: int, nz: int, dirs, weights,
+                   tol: float = 1e-3, max_iter: int = 200, accelerated: bool = False, W: int = 8, max_mip: int = 3,
+                   iod: float = 1e-2, chi_ds_min: float = 0.25, band=None, storage: int = STORE_F32,
+                   n_iter: int | None = None):
+    """MALI from LTE (Section 4.1): [eta, chi -> formal solution -> preconditioned
+    rates -> SE] until the largest relative population change is below ``tol``
+    (or exactly ``n_iter`` updates when given).
+
+    Every step is a library call; this function only sequences them (the formal
+    solution as in :func:`lambda_iteration`) and reads one number per iteration,
+    the convergence measure.  Returns ``(pops, n_updates, history)``.
+    """
+    n = nx * nz
+    L = int(np.asarray(lam_nm).size)
+    pops = lte_populations(ctx, atom, T, nh)
+    new = torch.empty_like(pops)
+    eta = torch.empty((L, n), dtype=torch.float32, device=T.device)
+    chi = torch.empty_like(eta)
+    J = torch.empty_like(eta)
+    rho = jeff = None
+    grid = mips = planes = probes = Jp = None
+    change = torch.empty(1, dtype=torch.float64, device=T.device)
+    hist = []
+    limit = max_iter if n_iter is None else n_iter
+    for it in range(limit):
+        atom_eta_chi(ctx, atom, lam_nm, tag, T, ne, pops, eta, chi)
+        grid = grid_build(ctx, nx, nz, eta, chi, out=grid)
+        ctx.set_own_cell(False)   # the solves return Jext
+        try:
+            if accelerated:
+                mips = mips_build(ctx, grid, eta, chi, W, max_mip, iod, iod, chi_ds_min, out=mips, storage=storage)
+                formal_solve_hdda(ctx, grid, mips, dirs, weights, J=J, band=band)
+            else:
+                if probes is None:
+                    off = grid.block_offset.view(grid.nbz, grid.nbx) >= 0
+                    cell = off.repeat_interleave(BLOCK, 0).repeat_interleave(BLOCK, 1).reshape(-1)
+                    probes = torch.nonzero(cell).to(torch.int32).reshape(-1)
+                    Jp = torch.empty((L, probes.numel()), dtype=torch.float32, device=T.device)
+                planes = pack_planes(ctx, eta, chi, W, out=planes)
+                formal_solve_dense(ctx, nx, nz, L, W, planes, dirs, weights, probes=probes, J=Jp)
+                J.zero_()
+                J[:, probes.long()] = Jp
+        finally:
+            ctx.set_own_cell(True)
+        rho, jeff = mali_rates(ctx, atom, lam_nm, tag, T, ne, pops, J, dirs, weights, rho=rho, jeff=jeff)
+        new = se_solve_preconditioned(ctx, atom, T, ne, nh, rho, jeff, out=new)
+        max_rel_change(ctx, T, pops, new, out=change)
+        hist.append(float(change.item()))
+        pops, new = new, pops
+        if n_iter is None and hist[-1] < tol:
+            return pops, it + 1, hist
+    return pops, limit, hist
 
 
 def voigt(ctx: Context, a: torch.Tensor, x: torch.Tensor, out=None):

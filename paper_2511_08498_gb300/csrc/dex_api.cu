@@ -1,4 +1,5 @@
 // C-ABI entry points of libdexgb: argument checks, context, launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -13,6 +14,7 @@ struct dex_ctx {
     cudaStream_t stream;
     unsigned int* status;  // device word, OR of DEX_ERR_* bits raised by kernels
     int traversal = DEX_TRAVERSAL_PER_BATCH;  // static accelerated solve: one walk per wavelength batch
+    int own_cell = 1;                          // solvers include each probe's own-cell emission
     char msg[512];
 };
 
@@ -210,6 +212,21 @@ int dex_ctx_set_traversal(dex_ctx* ctx, int mode)
     return ok(ctx);
 }
 
+int dex_ctx_set_own_cell(dex_ctx* ctx, int include)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (include != 0 && include != 1) return fail(ctx, DEX_ERR_ARG, "include must be 0 or 1");
+    ctx->own_cell = include;
+    return ok(ctx);
+}
+
+// solvers without the own-cell option refuse to run while it is off
+static int own_cell_required(dex_ctx* ctx, const char* who)
+{
+    if (ctx->own_cell) return DEX_OK;
+    return fail(ctx, DEX_ERR_UNSUPPORTED, "%s always includes the own-cell emission (dex_ctx_set_own_cell)", who);
+}
+
 int dex_ctx_set_stream(dex_ctx* ctx, void* stream)
 {
     if (!ctx) return DEX_ERR_ARG;
@@ -276,6 +293,7 @@ int dex_formal_solve_dense(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, co
     }
     if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
     dex::DenseParams P{};
+    P.exclude_own = ctx->own_cell ? 0 : 1;
     if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
     if (n_lambda == 0 || n_probe == 0) return ok(ctx);
     if (!planes || !J) return fail(ctx, DEX_ERR_ARG, "planes and J are required");
@@ -439,6 +457,10 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     P.storage = storage;
     P.n_band = -1;
     P.traversal = kind == 0 ? ctx->traversal : DEX_TRAVERSAL_PER_BATCH;
+    P.exclude_own = ctx->own_cell ? 0 : 1;
+    if (P.exclude_own && (kind != 0 || W != 8 || storage != DEX_STORE_F32))
+        return fail(ctx, DEX_ERR_UNSUPPORTED,
+                    "leaving out the own-cell emission needs the static solve with W = 8 and float32 bricks");
     if (band != nullptr && n_band >= 0) {
         if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);
         for (int q = 0; q < n_band; ++q) {
@@ -561,11 +583,87 @@ int dex_se_solve(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* t
         r = fail(ctx, DEX_ERR_ARG, "null buffer");
     if (!r) r = bind(ctx);
     if (!r) {
-        cudaError_t e = dex::launch_se_solve(ctx->stream, *P, n_cells, temperature, ne, nh, jbar, pops);
+        cudaError_t e = dex::launch_se_solve(ctx->stream, *P, n_cells, temperature, ne, nh, jbar, nullptr, pops);
         r = e != cudaSuccess ? cuda_fail(ctx, e, "se_solve launch") : ok(ctx);
     }
     delete P;
     return r;
+}
+
+int dex_mali_rates(dex_ctx* ctx, const dex_atom* atom, int n_cells, int n_lambda, const double* lambda_nm,
+                   const int* line_tag, const float* temperature, const float* ne, const double* pops, const float* J,
+                   int n_dir, const float* dirs, const float* weights, double* rho, double* jeff)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    dex::AtomParams* P = new (std::nothrow) dex::AtomParams();
+    dex::OwnCellOperator* O = new (std::nothrow) dex::OwnCellOperator();
+    int r = (!P || !O) ? fail(ctx, DEX_ERR_ARG, "host allocation failed") : DEX_OK;
+    if (!r) r = fill_atom(ctx, atom, n_lambda, lambda_nm, line_tag, *P);
+    if (!r && n_cells < 0) r = fail(ctx, DEX_ERR_ARG, "negative n_cells");
+    if (!r && n_cells > 0 && atom->n_line > 0 && (!temperature || !ne || !pops || !J || !rho || !jeff))
+        r = fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!r) {
+        dex::Quadrature* q = new (std::nothrow) dex::Quadrature();
+        if (!q) r = fail(ctx, DEX_ERR_ARG, "host allocation failed");
+        else r = fill_quadrature(ctx, n_dir, dirs, weights, *q);
+        if (!r) {
+            // group the directions by their own-cell path l = 1 / (2 max(|dx|, |dz|))
+            O->n = 0;
+            for (int k = 0; k < n_dir; ++k) {
+                const float ell = 0.5f / std::max(std::fabs(q->dx[k]), std::fabs(q->dz[k]));
+                int g = 0;
+                while (g < O->n && O->ell[g] != ell) ++g;
+                if (g == O->n) {
+                    O->ell[g] = ell;
+                    O->w[g] = 0.0f;
+                    ++O->n;
+                }
+                O->w[g] += q->w[k];
+            }
+        }
+        delete q;
+    }
+    if (!r) r = bind(ctx);
+    if (!r) {
+        cudaError_t e = dex::launch_mali_rates(ctx->stream, *P, *O, n_cells, temperature, ne, pops, J, rho, jeff);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "mali_rates launch") : ok(ctx);
+    }
+    delete P;
+    delete O;
+    return r;
+}
+
+int dex_se_solve_preconditioned(dex_ctx* ctx, const dex_atom* atom, int n_cells, const float* temperature,
+                                const float* ne, const float* nh, const double* rho, const double* jeff, double* pops)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    dex::AtomParams* P = new (std::nothrow) dex::AtomParams();
+    if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    int r = fill_atom(ctx, atom, 0, nullptr, nullptr, *P);
+    if (!r && n_cells < 0) r = fail(ctx, DEX_ERR_ARG, "negative n_cells");
+    if (!r && n_cells > 0 && (!temperature || !ne || !nh || !pops || (atom->n_line > 0 && (!rho || !jeff))))
+        r = fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!r) r = bind(ctx);
+    if (!r) {
+        cudaError_t e = dex::launch_se_solve(ctx->stream, *P, n_cells, temperature, ne, nh, jeff, rho, pops);
+        r = e != cudaSuccess ? cuda_fail(ctx, e, "se_solve launch") : ok(ctx);
+    }
+    delete P;
+    return r;
+}
+
+int dex_max_rel_change(dex_ctx* ctx, int n_level, int n_cells, const float* temperature, const double* old_pops,
+                       const double* new_pops, double* out)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (n_level < 1 || n_level > DEX_MAX_LEVELS) return fail(ctx, DEX_ERR_ARG, "n_level must be in [1, %d]", DEX_MAX_LEVELS);
+    if (n_cells < 0) return fail(ctx, DEX_ERR_ARG, "negative n_cells");
+    if (!out || (n_cells > 0 && (!temperature || !old_pops || !new_pops))) return fail(ctx, DEX_ERR_ARG, "null buffer");
+    if (!aligned(out, 8)) return fail(ctx, DEX_ERR_ARG, "out must be 8-byte aligned");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::launch_max_rel_change(ctx->stream, n_level, n_cells, temperature, old_pops, new_pops, out);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "max_rel_change launch");
+    return ok(ctx);
 }
 
 int dex_voigt(dex_ctx* ctx, int n, const float* a, const float* x, float* h)
@@ -870,6 +968,7 @@ static int batch_launch(dex_ctx* ctx, dex::BatchParams& P, const dex_batch_item*
                         size_t max_words, unsigned int* queue, unsigned long long* done_ns,
                         unsigned long long* start_ns)
 {
+    if (int r = own_cell_required(ctx, "the batched solve")) return r;
     P.queue = queue;
     P.done_ns = done_ns;
     P.start_ns = start_ns;
@@ -1045,6 +1144,7 @@ int dex_formal_solve_dense3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, 
                             float i_bc, float* J, float* I, unsigned long long* seg_count)
 {
     if (!ctx) return DEX_ERR_ARG;
+    if (int r = own_cell_required(ctx, "the 3D plain solve")) return r;
     if (int r = check_extent3(ctx, nx, ny, nz, false)) return r;
     if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
     if (n_lambda < 0) return fail(ctx, DEX_ERR_ARG, "negative n_lambda");
@@ -1178,6 +1278,7 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
                            unsigned long long* seg_count)
 {
     if (!ctx) return DEX_ERR_ARG;
+    if (int r = own_cell_required(ctx, "the 3D accelerated solve")) return r;
     if (int r = check_extent3(ctx, nx, ny, nz, true)) return r;
     if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
     if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");
@@ -1253,6 +1354,7 @@ int dex_rc_solve(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip,
                  unsigned long long* seg_count)
 {
     if (!ctx) return DEX_ERR_ARG;
+    if (int r = own_cell_required(ctx, "the cascade solve")) return r;
     if (int r = check_sparse_grid(ctx, nx, nz)) return r;
     if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
     if (n_lambda < 1) return fail(ctx, DEX_ERR_ARG, "n_lambda must be >= 1");

@@ -11,6 +11,7 @@ namespace dex {
 
 struct DenseParams {
     int nx, nz, n_lambda, W, n_batch;
+    int exclude_own;        // leave out each probe's own-cell emission (the first segment)
     long long n_cells;
     const float* planes;
     int n_probe;
@@ -41,6 +42,7 @@ struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
     int traversal;   // DEX_TRAVERSAL_PER_BATCH or DEX_TRAVERSAL_SHARED (static model, W = 8)
+    int exclude_own; // leave out each probe's own-voxel emission (static model, W = 8, float32)
     float band[4];
     long long n_cells;
     const float* bricks;
@@ -74,7 +76,20 @@ cudaError_t launch_atom_eta_chi(cudaStream_t s, const AtomParams& P, long long n
 cudaError_t launch_rates(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T, const float* J,
                          double* jbar);
 cudaError_t launch_se_solve(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T, const float* ne,
-                            const float* nh, const double* jbar, double* pops);
+                            const float* nh, const double* jbar, const double* rho, double* pops);
+
+// Directions grouped by the path from a cell centre to its boundary,
+// l = 1 / (2 max(|d_x|, |d_z|)) cells, with the summed quadrature weight of each group
+struct OwnCellOperator {
+    int n;
+    float ell[DEX_MAX_DIRS];
+    float w[DEX_MAX_DIRS];
+};
+cudaError_t launch_mali_rates(cudaStream_t s, const AtomParams& P, const OwnCellOperator& O, long long n_cells,
+                              const float* T, const float* ne, const double* pops, const float* J, double* rho,
+                              double* jeff);
+cudaError_t launch_max_rel_change(cudaStream_t s, int n_level, long long n_cells, const float* T, const double* old_p,
+                                  const double* new_p, double* out);
 
 // Core-and-Voigt: per-cell parameter fields (device pointers) and per-wavelength constants
 struct CavFields {

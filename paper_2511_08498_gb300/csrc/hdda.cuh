@@ -75,7 +75,8 @@ __device__ __forceinline__ int pack_block_info(int offset, int state) { return o
 // One ray from the centre of cell (i, j) (in active block a0 = (bx0, bz0), whose
 // level is mip0) along d = (dx, dz): accumulates I and T (initialised by the
 // caller) over the traversal; L looks up the batch's block states and offsets.
-template <int W, bool COUNT, class Model, class Lookup>
+// EXT: the emission of the probe's own voxel (the first segment) is left out.
+template <int W, bool COUNT, class Model, class Lookup, bool EXT = false>
 __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Params& M, int b, int i, int j,
                                           int bx0, int bz0, int a0, int mip0, float dx, float dz,
                                           const Lookup& L, float* I, float* T, unsigned int& nseg, bool& capped)
@@ -185,6 +186,12 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
             if constexpr (!Model::kEarlyLoad) cur = Model::load(cur_rp);
             const float nl2 = len * kNegLog2e;
             Model::integrate(M, cur, b, -dx, -dz, nl2, I, T);
+            if constexpr (EXT) {
+                if (it == 0) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) I[w] = 0.0f;
+                }
+            }
             if (COUNT) nseg += (th > th_prev);
         }
         if (last) break;
@@ -196,7 +203,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
 // kInfo: the CTA stages one word per block (offset * 8 + state, InfoLookup;
 // dynamic shared memory 4 * nbx * nbz bytes, grids of at most kInfoMaxBlocks
 // blocks); otherwise the packed state words (WordLookup; 8 * n_words bytes).
-template <int W, bool COUNT, class Model, bool kInfo = false>
+template <int W, bool COUNT, class Model, bool kInfo = false, bool EXT = false>
 __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const HddaParams P, const typename Model::Params M)
 {
     extern __shared__ unsigned long long s_dyn[];
@@ -249,11 +256,11 @@ __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const H
 #pragma unroll
         for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
         if constexpr (kInfo)
-            trace_ray<W, COUNT, Model>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz, InfoLookup{s_info}, I, T, nseg,
-                                       capped);
+            trace_ray<W, COUNT, Model, InfoLookup, EXT>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz,
+                                                        InfoLookup{s_info}, I, T, nseg, capped);
         else
-            trace_ray<W, COUNT, Model>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz,
-                                       WordLookup{s_dyn, P.block_offset}, I, T, nseg, capped);
+            trace_ray<W, COUNT, Model, WordLookup, EXT>(G, M, b, i, j, bx0, bz0, a0, mip0, dx, dz,
+                                                        WordLookup{s_dyn, P.block_offset}, I, T, nseg, capped);
         const float wk = P.quad.w[k];
 #pragma unroll
         for (int w = 0; w < W; ++w) {

@@ -12,7 +12,27 @@
 //  * k_se_solve      rate matrix (radiative + collisional, detailed balance)
 //                    and the per-cell statistical-equilibrium solve in float64,
 //                    ground row replaced by particle conservation; Gaussian
-//                    elimination with partial pivoting.
+//                    elimination with partial pivoting.  With rho given, the
+//                    downward radiative rate is A rho + B_ul Jbar (the MALI
+//                    preconditioned rate, rho = 1 - Psibar, Jbar = Jbar_eff).
+//  * k_mali_rates    MALI with same-transition preconditioning and the
+//                    diagonal operator of the long-characteristics solve
+//                    (Section 4.1, after Rybicki & Hummer 1992): per line and
+//                    cell, from the previous populations and their J,
+//                      rho      = 1 - Psibar
+//                               = sum_k w_k phi_k (E*_k chi_line,k + chi_c,k) / chi_k,
+//                      Jbar_eff = sum_k w_k phi_k (J_k - (1 - E*_k) eta_line,k / chi_k)
+//                               = sum_k w_k phi_k (Jext_k + (1 - E*_k) eta_c,k / chi_k),
+//                    E*_k = 1 - Lambda*_k = sum_d w_d e^{-chi_k l_d}, l_d the
+//                    path from the cell centre to its boundary along direction d,
+//                    Jext the formal solution with the probe's own-cell emission
+//                    left out (J = Jext + (1 - E*) (eta_line + eta_c) / chi).
+//                    Both forms avoid a cancellation: 1 - Psibar is not 1 minus a
+//                    sum near 1 (the profile has unit quadrature), and Jbar_eff is
+//                    not J minus the own-cell term, which in a cell thick at every
+//                    sampled frequency is J to float32 precision (that difference
+//                    stalled the iteration near 1e-2 in float32).
+//  * k_max_rel_change  max over non-empty cells and levels of |new - old| / new.
 #include "dex_internal.h"
 
 #include <cmath>
@@ -129,9 +149,75 @@ __global__ void k_rates(const AtomParams P, long long n_cells, const float* __re
     }
 }
 
+__global__ void k_mali_rates(const AtomParams P, const OwnCellOperator O, long long n_cells,
+                             const float* __restrict__ T_, const float* __restrict__ ne_,
+                             const double* __restrict__ pops, const float* __restrict__ Jext,
+                             double* __restrict__ rho, double* __restrict__ jeff)
+{
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        const double T = T_[c], ne = ne_[c];
+        const double chi_c = P.atom.background_sigma * ne * P.atom.cell_cm;
+        for (int li = 0; li < P.atom.n_line; ++li) {
+            double r = 0.0, je = 0.0;
+            if (T > 0.0) {
+                const double dnu = doppler_width(P, li, T);
+                const double norm = profile_norm(P, li, dnu);
+                const double nlo = pops[(long long)P.atom.line_lower[li] * n_cells + c];
+                const double nup = pops[(long long)P.atom.line_upper[li] * n_cells + c];
+                for (int k = 0; k < P.n_lambda; ++k) {
+                    if (P.tag[k] != li) continue;
+                    const double nu = P.nu[k];
+                    const double u = (nu - P.nu0[li]) / dnu;
+                    const double phi = exp(-u * u) / (kSqrtPi * dnu) * norm;
+                    const double f = kH * nu / (4.0 * kPi) * phi * P.atom.cell_cm;
+                    const double chi_l = f * (nlo * P.b_lu[li] - nup * P.b_ul[li]);
+                    const double chi = chi_l + chi_c;
+                    if (!(chi > 0.0)) continue;
+                    // escape from the own cell, summed over the direction groups
+                    const float xf = (float)chi;
+                    float es = 0.0f;
+                    for (int g = 0; g < O.n; ++g) es = fmaf(O.w[g], expf(-xf * O.ell[g]), es);
+                    const double e = (double)es;
+                    const double wp = P.wq[k] * phi;
+                    const double eta_c = chi_c * planck_nu(nu, T);
+                    r += wp * (e * chi_l + chi_c) / chi;
+                    je += wp * ((double)Jext[(long long)k * n_cells + c] + (1.0 - e) * eta_c / chi);
+                }
+            }
+            rho[(long long)li * n_cells + c] = r;
+            jeff[(long long)li * n_cells + c] = je;
+        }
+    }
+}
+
+// |new - old| / new maximised over non-empty cells and levels; positive doubles
+// order as their bit patterns, so the maximum is an integer atomicMax
+__global__ void k_max_rel_change(int n_level, long long n_cells, const float* __restrict__ T_,
+                                 const double* __restrict__ old_p, const double* __restrict__ new_p,
+                                 unsigned long long* __restrict__ out)
+{
+    double m = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (!(T_[c] > 0.0f)) continue;
+        for (int i = 0; i < n_level; ++i) {
+            const double a = old_p[(long long)i * n_cells + c], b = new_p[(long long)i * n_cells + c];
+            const double d = b > 0.0 ? fabs(b - a) / b : (a == b ? 0.0 : __longlong_as_double(0x7ff0000000000000LL));
+            m = d > m || d != d ? d : m;   // a NaN propagates
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double v = __shfl_down_sync(0xffffffffu, m, o);
+        m = v > m || v != v ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 __global__ void k_se_solve(const AtomParams P, long long n_cells, const float* __restrict__ T_,
                            const float* __restrict__ ne_, const float* __restrict__ nh_,
-                           const double* __restrict__ jbar, double* __restrict__ pops)
+                           const double* __restrict__ jbar, const double* __restrict__ rho,
+                           double* __restrict__ pops)
 {
     const int nl = P.atom.n_level;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n_cells;
@@ -155,7 +241,7 @@ __global__ void k_se_solve(const AtomParams P, long long n_cells, const float* _
             const int lo = P.atom.line_lower[li], up = P.atom.line_upper[li];
             const double jb = jbar[(long long)li * n_cells + c];
             R[lo][up] += P.b_lu[li] * jb;
-            R[up][lo] += P.atom.line_A[li] + P.b_ul[li] * jb;
+            R[up][lo] += P.atom.line_A[li] * (rho ? rho[(long long)li * n_cells + c] : 1.0) + P.b_ul[li] * jb;
         }
         // M n = b: row i = inflow - outflow of level i; row 0 = conservation
         double M[DEX_MAX_LEVELS][DEX_MAX_LEVELS + 1];
@@ -228,10 +314,29 @@ cudaError_t launch_rates(cudaStream_t s, const AtomParams& P, long long n_cells,
 }
 
 cudaError_t launch_se_solve(cudaStream_t s, const AtomParams& P, long long n_cells, const float* T, const float* ne,
-                            const float* nh, const double* jbar, double* pops)
+                            const float* nh, const double* jbar, const double* rho, double* pops)
 {
     if (n_cells == 0) return cudaSuccess;
-    k_se_solve<<<grid_for(n_cells), 128, 0, s>>>(P, n_cells, T, ne, nh, jbar, pops);
+    k_se_solve<<<grid_for(n_cells), 128, 0, s>>>(P, n_cells, T, ne, nh, jbar, rho, pops);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mali_rates(cudaStream_t s, const AtomParams& P, const OwnCellOperator& O, long long n_cells,
+                              const float* T, const float* ne, const double* pops, const float* J, double* rho,
+                              double* jeff)
+{
+    if (n_cells == 0 || P.atom.n_line == 0) return cudaSuccess;
+    k_mali_rates<<<grid_for(n_cells), 128, 0, s>>>(P, O, n_cells, T, ne, pops, J, rho, jeff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_rel_change(cudaStream_t s, int n_level, long long n_cells, const float* T, const double* old_p,
+                                  const double* new_p, double* out)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    if (e != cudaSuccess || n_cells == 0) return e;
+    k_max_rel_change<<<grid_for(n_cells), 256, 0, s>>>(n_level, n_cells, T, old_p, new_p,
+                                                       reinterpret_cast<unsigned long long*>(out));
     return cudaGetLastError();
 }
 

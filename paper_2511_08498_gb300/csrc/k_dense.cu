@@ -50,7 +50,11 @@ __global__ void k_pack_planes(long long n_cells, int n_lambda, int W, int n_batc
     }
 }
 
-template <int W, bool COUNT>
+// EXT: the probe's own-cell emission (the first segment of every ray) is left
+// out, so I and J hold the radiation arriving from beyond the cell, attenuated
+// by it -- the part of J that MALI's effective mean intensity needs without
+// subtracting the own-cell term from J (Section 4.1's preconditioning)
+template <int W, bool COUNT, bool EXT = false>
 __global__ void __launch_bounds__(256, 4) k_solve_dense(const DenseParams P)
 {
     const int b = blockIdx.y;
@@ -124,6 +128,12 @@ __global__ void __launch_bounds__(256, 4) k_solve_dense(const DenseParams P)
             const float len = fmaxf((th - th_prev) + (tl - tl_prev), 0.0f);
             const float nl2 = len * kNegLog2e;
             segments<W>(r.S, r.chi, nl2, I, T);
+            if constexpr (EXT) {
+                if (it == 0) {
+#pragma unroll
+                    for (int w = 0; w < W; ++w) I[w] = 0.0f;
+                }
+            }
             if (COUNT) nseg += (th > th_prev);
             if (th >= t2) break;
             // early termination every 16 cells once every transmission is exactly zero
@@ -158,8 +168,14 @@ __global__ void __launch_bounds__(256, 4) k_solve_dense(const DenseParams P)
 template <int W>
 void launch_dense_w(dim3 grid, cudaStream_t s, const DenseParams& P)
 {
-    if (P.seg_count) k_solve_dense<W, true><<<grid, 256, 0, s>>>(P);
-    else k_solve_dense<W, false><<<grid, 256, 0, s>>>(P);
+    if (P.exclude_own) {
+        if (P.seg_count) k_solve_dense<W, true, true><<<grid, 256, 0, s>>>(P);
+        else k_solve_dense<W, false, true><<<grid, 256, 0, s>>>(P);
+    } else if (P.seg_count) {
+        k_solve_dense<W, true><<<grid, 256, 0, s>>>(P);
+    } else {
+        k_solve_dense<W, false><<<grid, 256, 0, s>>>(P);
+    }
 }
 
 }  // namespace

@@ -66,6 +66,22 @@ cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& P)
 {
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
     if (solve_hdda_shared_applies(P)) return launch_solve_hdda_shared(s, P);
+    if (P.exclude_own) {
+        // own-voxel emission left out: W = 8, float32 records (the MALI path)
+        if (P.W != 8 || P.storage != kStoreF32) return cudaErrorNotSupported;
+        const long long nb = (long long)P.nbx * P.nbz;
+        const bool inf = nb <= kInfoMaxBlocks;
+        const size_t sm = inf ? sizeof(int) * (size_t)nb : sizeof(unsigned long long) * (size_t)P.n_words;
+        dim3 g((unsigned)P.cap_active, (unsigned)P.n_batch);
+        using SM8 = StaticModel<8, kStoreF32>;
+        cudaError_t e;
+        if (inf && P.seg_count) e = launch_hdda_kernel(k_solve_hdda_t<8, true, SM8, true, true>, g, sm, s, P, SM8::Params{});
+        else if (inf) e = launch_hdda_kernel(k_solve_hdda_t<8, false, SM8, true, true>, g, sm, s, P, SM8::Params{});
+        else if (P.seg_count) e = launch_hdda_kernel(k_solve_hdda_t<8, true, SM8, false, true>, g, sm, s, P, SM8::Params{});
+        else e = launch_hdda_kernel(k_solve_hdda_t<8, false, SM8, false, true>, g, sm, s, P, SM8::Params{});
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     // W = 8 on grids of at most kInfoMaxBlocks blocks: one shared-memory word per
     // block (InfoLookup); otherwise the packed state words (WordLookup)
     const long long n_blocks = (long long)P.nbx * P.nbz;

@@ -367,7 +367,7 @@ cudaError_t launch_mb(cudaStream_t s, const HddaParams& P)
 bool solve_hdda_shared_applies(const HddaParams& P)
 {
     const long long n_blocks = (long long)P.nbx * P.nbz;
-    return P.traversal == DEX_TRAVERSAL_SHARED && P.W == 8 && P.n_batch >= 2 && n_blocks <= kMbMaxBlocks &&
+    return P.traversal == DEX_TRAVERSAL_SHARED && !P.exclude_own && P.W == 8 && P.n_batch >= 2 && n_blocks <= kMbMaxBlocks &&
            P.cap_active < (1 << (31 - kMbStateBits));
 }
 
