@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-populations", action="store_true", help="skip the population-error check")
+    ap.add_argument("--no-moving", action="store_true", help="skip the moving-medium report")
     ap.add_argument("--nx", type=int, default=1024, help="grid side (smaller sides for profiling captures)")
     ap.add_argument("--phase", default="all", choices=["all", "accel", "plain"],
                     help="accel/plain: time only that path (profiling captures)")
@@ -456,6 +457,12 @@ def native(args):
     if not args.no_populations and args.phase == "all":
         out["populations"] = population_check(ctx, torch)
         out["mali"] = mali_check(ctx, torch)
+    if not args.no_moving and args.phase == "all":
+        # the moving-medium workload (2048 x 1024, 64 wavelengths, 64 directions): Core and
+        # Voigt at full resolution, and both treatments of Section 3 with VLM under three
+        # level tests (see paper_2511_08498_gb300.moving)
+        from paper_2511_08498_gb300 import moving
+        out["moving"] = moving.report(reps=1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, probes.cpu().numpy())
     if rank == 0:

@@ -233,6 +233,12 @@ typedef struct {
     int max_mip;       /* highest level, 0..4 (0: sparse skipping only)                   */
     int log_mean;      /* 1: log-space (geometric) mean of the children; 0: box filter     */
     int storage;       /* DEX_STORE_F32 / _BF16 / _F16 record format of the bricks         */
+    int n_test_dirs;   /* moving-medium builds: 0 = the level test of Sections 3.1 / 3.2
+                          alone; K in 1..16 = a group must also pass the IoD test on its
+                          children's emissivity and opacity as a ray along each of K
+                          in-plane propagation directions w_k = (cos 2 pi k / K,
+                          sin 2 pi k / K) samples them (see dex_cav_mips_build);
+                          ignored by the static builds                                     */
 } dex_vlm_params;
 
 /*

@@ -79,22 +79,43 @@ def param_chain(P0, max_mip):
     return chain
 
 
+def test_directions(n_test_dirs):
+    """The K in-plane propagation directions of the directional level test."""
+    th = 2.0 * np.pi * np.arange(n_test_dirs) / max(n_test_dirs, 1)
+    return list(zip(np.cos(th), np.sin(th)))
+
+
 def block_levels(chain, dv, c_kms, empty, block, lambda_batch, thr_eta, thr_chi, chi_ds_min=0.25,
-                 method="hum1wei24", stats=False):
-    """Per-batch block levels from the closest-to-core IoD test over the chain's children."""
+                 method="hum1wei24", stats=False, n_test_dirs=0):
+    """Per-batch block levels from the closest-to-core IoD test over the chain's children.
+
+    With ``n_test_dirs`` = K > 0 (a reading of the "worst-case gradients" the test
+    is meant to bound) a group must also pass the same test on its children
+    evaluated as a ray propagating along each w_k = (cos 2 pi k / K, sin 2 pi k / K)
+    samples them: u = dv + v_child . w_k.  ``stats``: per level a dict of the
+    closest-to-core test's quantities; with K > 0 a list of such per-level lists,
+    one per evaluation (closest-to-core first, then the K directions)."""
     max_mip = len(chain) - 1
-    passes, st = [], []
+    passes = []
+    st = [[] for _ in range(1 + n_test_dirs)]
     for m in range(1, max_mip + 1):
         ds = float(2 ** m)
-        e, x = eta_chi(chain[m - 1], dv, 0.0, 0.0, c_kms, method=method, closest_to_core=True)
-        ge, gx = omips._groups(e), omips._groups(x)
-        _, iod_e = omips._reduce(ge, ds, "linear")
-        _, iod_c = omips._reduce(gx, ds, "linear")
-        kds = gx.max(-1) * ds
-        passes.append(((iod_e < thr_eta) & (iod_c < thr_chi)) | (kds < chi_ds_min))
-        st.append({"iod_eta": iod_e, "iod_chi": iod_c, "chi_ds": kds})
+        evals = [eta_chi(chain[m - 1], dv, 0.0, 0.0, c_kms, method=method, closest_to_core=True)]
+        evals += [eta_chi(chain[m - 1], dv, wx, wz, c_kms, method=method) for wx, wz in test_directions(n_test_dirs)]
+        ok = None
+        for q, (e, x) in enumerate(evals):
+            ge, gx = omips._groups(e), omips._groups(x)
+            _, iod_e = omips._reduce(ge, ds, "linear")
+            _, iod_c = omips._reduce(gx, ds, "linear")
+            kds = gx.max(-1) * ds
+            p = ((iod_e < thr_eta) & (iod_c < thr_chi)) | (kds < chi_ds_min)
+            ok = p if ok is None else ok & p
+            st[q].append({"iod_eta": iod_e, "iod_chi": iod_c, "chi_ds": kds})
+        passes.append(ok)
     lev = omips.block_levels(passes, empty, block, lambda_batch, n_lambda=np.asarray(dv).size)
-    return (lev, st) if stats else lev
+    if not stats:
+        return lev
+    return lev, (st[0] if n_test_dirs == 0 else st)
 
 
 def formal_solve(P_levels, level_map, block, lambda_batch, dv, c_kms, dirs, weights, probes, band=None,

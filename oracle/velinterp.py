@@ -107,8 +107,33 @@ def formal_solve(grids, level_map, block, lambda_batch, dirs, weights, probes, b
     return (J, I) if want_intensity else J
 
 
-def levels(P0, dv, c_kms, empty, block, lambda_batch, max_mip, thr, chi_ds_min=0.25, stats=False):
+def levels(P0, dv, c_kms, empty, block, lambda_batch, max_mip, thr, chi_ds_min=0.25, stats=False, n_test_dirs=0):
+    """Per-batch block levels from the rest-frame IoD test (Section 3.1).
+
+    With ``n_test_dirs`` = K > 0 a group must also pass the same test on its
+    children's velocity grids interpolated as a ray propagating along each
+    w_k = (cos 2 pi k / K, sin 2 pi k / K) samples them (a reading, as in
+    ``oracle.cav.block_levels``); ``stats`` as there."""
     e0, x0 = rest_frame(P0, dv, c_kms)
     res = omips.mip_chain(e0, x0, max_mip, thr, thr, chi_ds_min, mean="linear", stats=True)
-    lev = omips.block_levels(res[1], empty, block, lambda_batch, n_lambda=np.asarray(dv).size)
-    return (lev, res[2]) if stats else lev
+    passes = list(res[1])
+    st_all = [res[2]]
+    if n_test_dirs > 0 and max_mip > 0:
+        from .cav import test_directions
+        grids = velocity_grids(P0, dv, c_kms, max_mip - 1)
+        for wx, wz in test_directions(n_test_dirs):
+            st_d = []
+            for m in range(1, max_mip + 1):
+                ds = float(2 ** m)
+                e, x = interpolate(grids[m - 1], wx, wz)
+                ge, gx = omips._groups(e), omips._groups(x)
+                _, iod_e = omips._reduce(ge, ds, "linear")
+                _, iod_c = omips._reduce(gx, ds, "linear")
+                kds = gx.max(-1) * ds
+                passes[m - 1] = passes[m - 1] & (((iod_e < thr) & (iod_c < thr)) | (kds < chi_ds_min))
+                st_d.append({"iod_eta": iod_e, "iod_chi": iod_c, "chi_ds": kds})
+            st_all.append(st_d)
+    lev = omips.block_levels(passes, empty, block, lambda_batch, n_lambda=np.asarray(dv).size)
+    if not stats:
+        return lev
+    return lev, (st_all[0] if n_test_dirs == 0 else st_all)

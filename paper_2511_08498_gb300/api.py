@@ -140,7 +140,8 @@ STATES_PER_WORD = 21
 class VlmParams(ctypes.Structure):
     """``dex_vlm_params``: variance-limited mipmapping thresholds (Section 2.2)."""
     _fields_ = [("iod_eta", ctypes.c_float), ("iod_chi", ctypes.c_float), ("chi_ds_min", ctypes.c_float),
-                ("max_mip", ctypes.c_int), ("log_mean", ctypes.c_int), ("storage", ctypes.c_int)]
+                ("max_mip", ctypes.c_int), ("log_mean", ctypes.c_int), ("storage", ctypes.c_int),
+                ("n_test_dirs", ctypes.c_int)]
 
 
 STORE_F32, STORE_BF16, STORE_F16 = 0, 1, 2
@@ -535,7 +536,7 @@ def cav_grid_build(ctx: Context, nx: int, nz: int, fields: dict, out: SparseGrid
 
 def cav_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: float, W: int, max_mip: int,
                    iod_eta: float, iod_chi: float, chi_ds_min: float = 0.25, level_cap=None, capacity=None,
-                   out: CavMips | None = None):
+                   out: CavMips | None = None, test_dirs: int = 0):
     cap = grid.n_blocks if capacity is None else int(capacity)
     dvh = np.ascontiguousarray(np.asarray(dv, dtype=np.float32))
     n_batch = -(-dvh.size // W)
@@ -546,7 +547,7 @@ def cav_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: floa
                       torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=dev),
                       W, max_mip, dvh, c_kms, cap)
     f = CavFields.from_tensors(fields)
-    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0, STORE_F32)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0, STORE_F32, int(test_dirs))
     fp = ctypes.POINTER(ctypes.c_float)
     ctx._rc(lib().dex_cav_mips_build(ctx.handle, grid.nx, grid.nz, ctypes.byref(f), dvh.size, W,
                                      dvh.ctypes.data_as(fp), float(c_kms), _ptr(grid.active), _ptr(grid.n_active_dev),
@@ -595,7 +596,7 @@ VEL_SAMPLES = 8
 
 def vel_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: float, W: int, max_mip: int,
                    iod_eta: float, iod_chi: float, chi_ds_min: float = 0.25, level_cap=None, capacity=None,
-                   out: CavMips | None = None):
+                   out: CavMips | None = None, test_dirs: int = 0):
     """Velocity-grid MIP chains + rest-frame VLM levels (``dex_vel_mips_build``)."""
     cap = grid.n_blocks if capacity is None else int(capacity)
     dvh = np.ascontiguousarray(np.asarray(dv, dtype=np.float32))
@@ -607,7 +608,7 @@ def vel_mips_build(ctx: Context, grid: SparseGrid, fields: dict, dv, c_kms: floa
                       torch.empty((n_batch, state_words(grid.nx, grid.nz)), dtype=torch.int64, device=dev),
                       W, max_mip, dvh, c_kms, cap)
     f = CavFields.from_tensors(fields)
-    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0, STORE_F32)
+    p = VlmParams(float(iod_eta), float(iod_chi), float(chi_ds_min), int(max_mip), 0, STORE_F32, int(test_dirs))
     fp = ctypes.POINTER(ctypes.c_float)
     ctx._rc(lib().dex_vel_mips_build(ctx.handle, grid.nx, grid.nz, ctypes.byref(f), dvh.size, W,
                                      dvh.ctypes.data_as(fp), float(c_kms), _ptr(grid.active), _ptr(grid.n_active_dev),

@@ -751,6 +751,14 @@ static int moving_mips_build(dex_ctx* ctx, bool velgrid, int nx, int nz, const d
     P.thr_eta = params->iod_eta;
     P.thr_chi = params->iod_chi;
     P.chi_ds_min = params->chi_ds_min;
+    if (params->n_test_dirs < 0 || params->n_test_dirs > dex::kMaxTestDirs)
+        return fail(ctx, DEX_ERR_ARG, "n_test_dirs must be in [0, %d]", dex::kMaxTestDirs);
+    P.n_test_dirs = params->n_test_dirs;
+    for (int k = 0; k < P.n_test_dirs; ++k) {
+        const double th = 2.0 * 3.14159265358979323846 * (double)k / (double)P.n_test_dirs;
+        P.test_wx[k] = (float)std::cos(th);
+        P.test_wz[k] = (float)std::sin(th);
+    }
     P.active = active;
     P.n_active = n_active;
     P.level_cap = level_cap;

@@ -118,9 +118,14 @@ struct CavMlpParams {
     float w[4481];
 };
 
+constexpr int kMaxTestDirs = 16;
+
 struct CavMipParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active;
     float thr_eta, thr_chi, chi_ds_min;
+    int n_test_dirs;                   // directional level tests (0: the paper's test alone)
+    float test_wx[kMaxTestDirs];       // their propagation directions
+    float test_wz[kMaxTestDirs];
     CavFields F;
     const int* active;
     const int* n_active;

@@ -16,6 +16,10 @@
 // its speed allows, |u| = max(0, |dv| - |v|) -- is below the thresholds, or the
 // largest such chi Ds is below chi_ds_min; the block level is the largest m with
 // every group of every level <= m passing for every wavelength of the batch.
+// With n_test_dirs = K > 0 a group must also pass the same test on its children
+// evaluated as a ray along each w_k samples them, u = dv + v_child . w_k: the
+// closest-to-core values of children moving in different directions can agree
+// while the profiles a ray sees are shifted apart.
 #include "hdda.cuh"
 #include "mlp.cuh"
 #include "vlm.cuh"
@@ -111,7 +115,10 @@ struct CavModel {
                                                      float nl2, float* I, float* T)
     {
         const float proj = fmaf(v.p[4], wx, v.p[5] * wz);
-#pragma unroll
+        // not unrolled: eight inlined copies of the four-branch Voigt evaluation made
+        // the solve instruction-fetch bound (1024 x 512, 64 wavelengths: 9.4 s against
+        // 2.3 s with one copy; bit-identical)
+#pragma unroll 1
         for (int w = 0; w < W; ++w) {
             const int l = b * W + w;
             float eta, chi;
@@ -210,6 +217,19 @@ __global__ void __launch_bounds__(256) k_cav_mips_build(const CavMipParams P, co
                 const GroupStat sc = reduce_group(x[0], x[1], x[2], x[3], ln_ds, false);
                 const float kmax = fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3]));
                 pass = pass && ((se.iod < P.thr_eta && sc.iod < P.thr_chi) || (kmax * ds < P.chi_ds_min));
+                // directional tests: the children as a ray propagating along w_k samples them,
+                // each at its own (mean) velocity projected on w_k
+                for (int d = 0; d < P.n_test_dirs && pass; ++d) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float* cp = sp[ch[k]];
+                        cav_eta_chi(M, cp, l, M.dv[l] + fmaf(cp[4], P.test_wx[d], cp[5] * P.test_wz[d]), e[k], x[k]);
+                    }
+                    const GroupStat de = reduce_group(e[0], e[1], e[2], e[3], ln_ds, false);
+                    const GroupStat dc = reduce_group(x[0], x[1], x[2], x[3], ln_ds, false);
+                    const float dmax = fmaxf(fmaxf(x[0], x[1]), fmaxf(x[2], x[3]));
+                    pass = (de.iod < P.thr_eta && dc.iod < P.thr_chi) || (dmax * ds < P.chi_ds_min);
+                }
             }
         }
         const int all = __syncthreads_and(pass ? 1 : 0);

@@ -8,7 +8,9 @@
 // (propagation w = -d) the voxel's eta, chi are the linear interpolation of its
 // grid at the projected velocity v_mean . w, clamped to [-V, V].  The level of a
 // block per batch comes from Eq. IoD on the rest-frame values (projected
-// velocity 0), Section 3.1, with the always-average rule.
+// velocity 0), Section 3.1, with the always-average rule; with n_test_dirs = K
+// > 0 also from the same test on the children's grids interpolated as a ray
+// along each of K in-plane directions samples them.
 #include "hdda.cuh"
 #include "vlm.cuh"
 #include "voigt.cuh"
@@ -173,6 +175,57 @@ __global__ void __launch_bounds__(256) k_vel_mips_build(const CavMipParams P, co
         }
     }
 
+    // directional tests (n_test_dirs = K > 0): a level that passed the rest-frame test
+    // must also pass it on its children as a ray along each w_k samples them -- each
+    // child's velocity grid interpolated at its mean velocity projected on w_k, as
+    // the traversal does -- since rest-frame values of children moving in different
+    // directions can agree while the profiles a ray sees are shifted apart
+    if (P.n_test_dirs > 0 && level > 0) {
+        __syncthreads();  // the grids above are written by the whole CTA
+        int dlevel = 0;
+        for (int m = 1; m <= level; ++m) {
+            const int side = DEX_BLOCK >> m, side_p = side << 1;
+            const int off_p = level_offset(m - 1);
+            const float ds = (float)(1 << m);
+            const float ln_ds = (float)m * 0.69314718f;
+            bool pass = true;
+            if (t < side * side) {
+                const int vx_ = t % side, vz_ = t / side;
+                const int c0 = off_p + (2 * vz_) * side_p + 2 * vx_;
+                const int ch[4] = {c0, c0 + 1, c0 + side_p, c0 + side_p + 1};
+                for (int d = 0; d < P.n_test_dirs && pass; ++d) {
+                    float e[4][W], x[4][W];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float* rec = brick + (size_t)ch[k] * REC;
+                        const float4 h = *reinterpret_cast<const float4*>(rec);
+                        const float proj = fminf(fmaxf(fmaf(h.x, P.test_wx[d], h.y * P.test_wz[d]), -h.z), h.z);
+                        const float f = h.z > 0.0f ? (proj + h.z) / (2.0f * h.z) * (float)(kNV - 1) : 0.0f;
+                        const int i0 = min((int)f, kNV - 2);
+                        const float u = f - (float)i0;
+                        const float* r0 = rec + 4 + i0 * 2 * W;
+                        const float* r1 = r0 + 2 * W;
+#pragma unroll
+                        for (int w = 0; w < W; ++w) {
+                            e[k][w] = fmaf(u, r1[w] - r0[w], r0[w]);
+                            x[k][w] = fmaf(u, r1[W + w] - r0[W + w], r0[W + w]);
+                        }
+                    }
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        if (b * W + w >= P.n_lambda) continue;
+                        const GroupStat se = reduce_group(e[0][w], e[1][w], e[2][w], e[3][w], ln_ds, false);
+                        const GroupStat sc = reduce_group(x[0][w], x[1][w], x[2][w], x[3][w], ln_ds, false);
+                        const float kmax = fmaxf(fmaxf(x[0][w], x[1][w]), fmaxf(x[2][w], x[3][w]));
+                        pass = pass && ((se.iod < P.thr_eta && sc.iod < P.thr_chi) || (kmax * ds < P.chi_ds_min));
+                    }
+                }
+            }
+            if (!__syncthreads_and(pass ? 1 : 0)) break;
+            dlevel = m;
+        }
+        level = dlevel;
+    }
     if (t == 0) {
         if (P.level_cap != nullptr) level = min(level, max((int)P.level_cap[blk], 0));
         const unsigned long long state = (unsigned long long)(level + 1);

@@ -4,8 +4,11 @@ Runs, on a 2048 x 1024 moving-medium atmosphere (64 wavelengths, 64 directions
 by default):
   * the Core-and-Voigt solve at full resolution (MIP 0 only, every probe of
     every non-empty block): the exact-profile reference of this report;
-  * Core and Voigt with VLM levels 0-3 and distance limits;
-  * velocity interpolation (8 stored velocity samples) with the same levels;
+  * Core and Voigt with VLM levels 0-3 and distance limits, and velocity
+    interpolation (8 stored velocity samples) with the same levels, each with
+    three level tests: the paper's (IoD plus the always-average rule for
+    chi Ds < 0.25), the IoD test alone, and the IoD test alone plus the test in
+    8 propagation directions;
   * optionally Core and Voigt with the learned profile (``--mlp PARAMS.npy``),
     on a reduced atmosphere because it evaluates the network per segment.
 Each is timed with CUDA events; J is compared with the reference (relative
@@ -65,8 +68,12 @@ def dense_seg_lambda(ctx, grid, n_lambda, W, dirs, w):
     return int(seg.item()) * -(-n_lambda // W) * W
 
 
+# level-test variants: (name suffix, always-average threshold chi_ds_min, directional tests K)
+LEVEL_TESTS = (("", 0.25, 0), ("_iod_only", 0.0, 0), ("_iod_only_dirtest8", 0.0, 8))
+
+
 def report(nx=2048, nz=1024, n_lambda=64, n_dir=64, W=8, max_mip=3, iod=1e-2, mlp_params=None, mlp_nx=256,
-           mlp_nz=128, reps=2):
+           mlp_nz=128, reps=2, level_tests=LEVEL_TESTS):
     import synth
     ctx = api.Context(0)
     m = synth.dynamic_line_atmosphere(nx, nz, n_lambda=n_lambda, seed=synth.SEED_BASE + 3)
@@ -83,18 +90,29 @@ def report(nx=2048, nz=1024, n_lambda=64, n_dir=64, W=8, max_mip=3, iod=1e-2, ml
            "dense_seg_lambda": dense,
            "cav_plain": {"ms": t_plain * 1e3, "seg_lambda_per_s": dense / t_plain}}
     Jc = torch.empty_like(ref)
-    cav = api.cav_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, 0.25)
-    t_cav = _time(lambda: api.formal_solve_cav(ctx, grid, cav, dirs, w, J=Jc, band=BAND), reps)
-    _, _, sc = api.formal_solve_cav(ctx, grid, cav, dirs, w, J=Jc, band=BAND, count_segments=True)
-    ctx.check()
-    out["cav_vlm"] = {"ms": t_cav * 1e3, "seg_lambda_per_s": dense / t_cav, "speedup_vs_plain": t_plain / t_cav,
-                      "executed_fraction": int(sc.item()) * W / dense, "j_err_pct_vs_plain": _err(Jc, ref)}
     Jv = torch.empty_like(ref)
-    vel = api.vel_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, 0.25)
-    t_vel = _time(lambda: api.formal_solve_velinterp(ctx, grid, vel, dirs, w, J=Jv, band=BAND), reps)
+    # velocity interpolation at full resolution: the error of interpolating the
+    # profile between the stored velocity samples, before any mipmapping
+    vel0 = api.vel_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, 0, iod, iod, 0.25)
+    t_vel0 = _time(lambda: api.formal_solve_velinterp(ctx, grid, vel0, dirs, w, J=Jv), reps)
     ctx.check()
-    out["velinterp_vlm"] = {"ms": t_vel * 1e3, "seg_lambda_per_s": dense / t_vel,
-                            "speedup_vs_plain": t_plain / t_vel, "j_err_pct_vs_plain": _err(Jv, ref)}
+    out["velinterp_mip0"] = {"ms": t_vel0 * 1e3, "speedup_vs_plain": t_plain / t_vel0,
+                             "j_err_pct_vs_plain": _err(Jv, ref)}
+    for tag, cm, K in level_tests:
+        cav = api.cav_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, cm, test_dirs=K)
+        t_cav = _time(lambda: api.formal_solve_cav(ctx, grid, cav, dirs, w, J=Jc, band=BAND), reps)
+        _, _, sc = api.formal_solve_cav(ctx, grid, cav, dirs, w, J=Jc, band=BAND, count_segments=True)
+        ctx.check()
+        lt = {"chi_ds_min": cm, "directional_tests": K}
+        out["cav_vlm" + tag] = {"ms": t_cav * 1e3, "seg_lambda_per_s": dense / t_cav,
+                                "speedup_vs_plain": t_plain / t_cav, "executed_fraction": int(sc.item()) * W / dense,
+                                "level_test": lt, "j_err_pct_vs_plain": _err(Jc, ref)}
+        vel = api.vel_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, cm, test_dirs=K)
+        t_vel = _time(lambda: api.formal_solve_velinterp(ctx, grid, vel, dirs, w, J=Jv, band=BAND), reps)
+        ctx.check()
+        out["velinterp_vlm" + tag] = {"ms": t_vel * 1e3, "seg_lambda_per_s": dense / t_vel,
+                                      "speedup_vs_plain": t_plain / t_vel, "level_test": lt,
+                                      "j_err_pct_vs_plain": _err(Jv, ref)}
     if mlp_params is not None:
         ms = synth.dynamic_line_atmosphere(mlp_nx, mlp_nz, n_lambda=n_lambda, seed=synth.SEED_BASE + 3)
         fs = {k: torch.from_numpy(np.ascontiguousarray(ms[k]).reshape(-1)).cuda() for k in api.CAV_FIELDS}

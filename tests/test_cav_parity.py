@@ -79,24 +79,26 @@ def model(nx=128, nz=96, n_lambda=16, seed=600):
     return synth.dynamic_line_atmosphere(nx, nz, n_lambda=n_lambda, seed=synth.SEED_BASE + seed)
 
 
-def gpu_cav(ctx, m, W, max_mip, iod, dirs, w, band=None, cm=0.25, mlp_params=None):
+def gpu_cav(ctx, m, W, max_mip, iod, dirs, w, band=None, cm=0.25, mlp_params=None, test_dirs=0):
     from paper_2511_08498_gb300 import api
     nz, nx = m["chi_c"].shape
     f = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda() for k in api.CAV_FIELDS}
     grid = api.cav_grid_build(ctx, nx, nz, f)
-    mp = api.cav_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, cm)
+    mp = api.cav_mips_build(ctx, grid, f, m["dv"], m["c_kms"], W, max_mip, iod, iod, cm, test_dirs=test_dirs)
     J, I, seg = api.formal_solve_cav(ctx, grid, mp, dirs, w, band=band, want_intensity=True, count_segments=True,
                                      mlp_params=mlp_params)
     ctx.check()
     return grid, mp, J, I, seg
 
 
-def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei24", stats=False, profile=None):
+def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei24", stats=False, profile=None,
+               test_dirs=0):
     P0 = cav.param_arrays(m)
     chain = cav.param_chain(P0, max_mip)
     empty = omips.block_empty(np.stack([m["eta_star"], m["eta_c"]]), np.stack([m["chi_star"], m["chi_c"]]), 16)
     if max_mip > 0:
-        lev, st = cav.block_levels(chain, m["dv"], m["c_kms"], empty, 16, W, iod, iod, cm, stats=True)
+        lev, st = cav.block_levels(chain, m["dv"], m["c_kms"], empty, 16, W, iod, iod, cm, stats=True,
+                                   n_test_dirs=test_dirs)
     else:
         lev, st = omips.block_levels([], empty, 16, W, n_lambda=m["dv"].size), []
     probes = omips.probes_of_blocks(empty, 16)
@@ -105,14 +107,21 @@ def oracle_cav(m, W, max_mip, iod, dirs, w, band=None, cm=0.25, method="hum1wei2
     return dict(lev=lev, stats=st, probes=probes, J=J, I=I, empty=empty)
 
 
-@pytest.mark.parametrize("max_mip,iod,band", [(0, 1.0, None), (2, 1.0, None), (3, 1e9, [5.3, 21.7, 40.2]),
-                                              (2, 1e-2, [3.1])])
-def test_cav_solve_matches_oracle(ctx, max_mip, iod, band):
+@pytest.mark.parametrize("max_mip,iod,band,cm,test_dirs", [(0, 1.0, None, 0.25, 0), (2, 1.0, None, 0.25, 0),
+                                                            (3, 1e9, [5.3, 21.7, 40.2], 0.25, 0),
+                                                            (2, 1e-2, [3.1], 0.25, 0),
+                                                            (3, 100.0, [5.3, 21.7, 40.2], 0.0, 8)])
+def test_cav_solve_matches_oracle(ctx, max_mip, iod, band, cm, test_dirs):
     from paper_2511_08498_gb300 import api
+    from levels_util import robust_level_mask_multi
     m = model()
     dirs, w = synth.directions(8)
-    grid, mp, J, I, seg = gpu_cav(ctx, m, 8, max_mip, iod, dirs, w, band=band)
-    o = oracle_cav(m, 8, max_mip, iod, dirs, w, band=band)
+    grid, mp, J, I, seg = gpu_cav(ctx, m, 8, max_mip, iod, dirs, w, band=band, cm=cm, test_dirs=test_dirs)
+    o = oracle_cav(m, 8, max_mip, iod, dirs, w, band=band, cm=cm, test_dirs=test_dirs)
+    if test_dirs:   # the directional tests change levels here, and no decision sits on a threshold
+        assert robust_level_mask_multi(o["stats"], o["lev"], 8, 16, max_mip, iod, iod, cm).all()
+        lev0 = oracle_cav(m, 8, max_mip, iod, dirs, w, band=band, cm=cm)["lev"]
+        assert (lev0 != o["lev"]).any()
     nbz, nbx = o["empty"].shape
     assert grid.n_active() == int((~o["empty"]).sum())
     glev = api.unpack_states(mp.words.cpu().numpy(), nbz * nbx).reshape(o["lev"].shape)
