@@ -545,6 +545,35 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
                     unsigned long long* done_ns, unsigned long long* start_ns);
 
 /*
+ * Launch configuration of the batched solve (the knobs an autotuner sweeps; no
+ * paper counterpart -- the paper batches wavelengths within one model, Section 4.1):
+ *   ctas     persistent grid size (0: 3 per SM)
+ *   packet   probes per work item: 256 (a whole block), 128 or 64 (a 16 x 8 or
+ *            16 x 4 part of it; the CTA then has that many threads)
+ *   chunk    work items a CTA claims per increment of the queue counter (1..64)
+ *   staging  how the CTA stages its atmosphere-batch's block table in shared
+ *            memory: 0 the packed 3-bit state words (plus the global offset
+ *            table), 1 one word per block, offset * 8 + state (every grid of
+ *            the batch at most 8192 blocks)
+ *   occupancy  0: the compiler's register budget; 1 (W = 8 only): 64 registers
+ *            a thread, so that 1024 threads a SM are resident (some spilling)
+ * Every probe accumulates J over the directions in one thread in the order of
+ * dex_formal_solve_hdda, so J is bit-identical for every configuration.
+ * dex_batch_solve is dex_batch_solve_config with {ctas, 256, 1, 0, 0}.  Invalid
+ * values -> DEX_ERR_ARG.
+ */
+typedef struct {
+    int ctas;
+    int packet;
+    int chunk;
+    int staging;
+    int occupancy;
+} dex_batch_config;
+
+int dex_batch_solve_config(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, const dex_batch_config* cfg,
+                           unsigned int* queue, unsigned long long* done_ns, unsigned long long* start_ns);
+
+/*
  * Allocation-free variant of dex_batch_solve (the paper has no counterpart:
  * this is a deployment convenience of this library).
  *

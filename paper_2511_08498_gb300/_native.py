@@ -71,6 +71,7 @@ PROTOTYPES = {
                                            c_void_p, c_void_p, c_int, c_int, c_fp, c_fp, c_int, c_fp, c_float,
                                            c_void_p, c_void_p, c_void_p]),
     "dex_batch_solve": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]),
+    "dex_batch_solve_config": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dex_batch_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "dex_measure_ex2_rate": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "dex_selftest_wait_timeout": (c_int, [c_void_p, c_int]),

@@ -689,6 +689,30 @@ def batch_solve(ctx: Context, items, W: int, ctas: int = 0, queue: torch.Tensor 
     return done, start
 
 
+class BatchConfig(ctypes.Structure):
+    """``dex_batch_config``: persistent grid size, probes per work item, items per
+    queue claim, block-table staging (0 packed state words, 1 one word per block)."""
+    _fields_ = [("ctas", ctypes.c_int), ("packet", ctypes.c_int), ("chunk", ctypes.c_int), ("staging", ctypes.c_int),
+                ("occupancy", ctypes.c_int)]
+
+
+def batch_solve_config(ctx: Context, items, W: int, ctas: int = 0, packet: int = 256, chunk: int = 1,
+                       staging: int = 0, occupancy: int = 0, queue: torch.Tensor | None = None,
+                       timing: bool = False):
+    """``dex_batch_solve_config``: the batched solve with an explicit launch configuration."""
+    n = len(items)
+    arr = (BatchItem * n)(*items)
+    dev = torch.device("cuda", ctx.device)
+    if queue is None:
+        queue = torch.zeros(1, dtype=torch.int32, device=dev)
+    done = torch.zeros(n, dtype=torch.int64, device=dev) if timing else None
+    start = torch.zeros(1, dtype=torch.int64, device=dev) if timing else None
+    cfg = BatchConfig(int(ctas), int(packet), int(chunk), int(staging), int(occupancy))
+    ctx._rc(lib().dex_batch_solve_config(ctx.handle, n, arr, W, ctypes.byref(cfg), _ptr(queue), _ptr(done),
+                                         _ptr(start)))
+    return done, start
+
+
 def batch_solve_noalloc(ctx: Context, items, W: int, ctas: int = 0, done_ns: torch.Tensor | None = None,
                         start_ns: torch.Tensor | None = None):
     """``dex_batch_solve_noalloc``: the batched solve for callers that cannot allocate

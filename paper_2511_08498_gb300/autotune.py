@@ -1,7 +1,9 @@
 """Autotuning and reporting of the batched (many-atmosphere) solve.
 
-``tune_batch`` times the persistent launch for several grid sizes (CTAs per SM)
-and returns the fastest; ``batch_report`` builds a seeded set of independent
+``tune_batch`` sweeps the persistent launch's knobs (grid size, probes per
+work item, items per queue claim, block-table staging, register budget) by
+coordinate descent; ``tune_threshold`` picks the fastest IoD threshold whose J
+error meets a bar; ``batch_report`` builds a seeded set of independent
 atmospheres, then times one step three ways -- a sequential launch per
 atmosphere, one persistent launch, and the whole step (line synthesis, grids,
 MIPs and the persistent solve) replayed from a captured CUDA graph -- and writes
@@ -39,15 +41,70 @@ def _time(fn, reps=3):
     return best
 
 
-def tune_batch(ctx, items, W, ctas_per_sm=(1, 2, 3, 4), reps=3):
-    """Fastest persistent grid size: returns ``{"best_ctas", "times_ms"}``."""
+def tune_batch(ctx, items, W, reps=3, rounds=2):
+    """Coordinate descent over the launch knobs of ``dex_batch_solve_config`` --
+    persistent grid size, probes per work item (packet), work items per queue
+    claim (chunk), block-table staging and register budget -- starting from the
+    default configuration; every knob is swept with the others fixed, twice.
+    Returns ``{"best", "best_ms", "default", "default_ms", "trials"}``."""
     sms = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     queue = torch.zeros(1, dtype=torch.int32, device=torch.device("cuda", ctx.device))
-    times = {}
-    for k in ctas_per_sm:
-        times[k * sms] = _time(lambda: api.batch_solve(ctx, items, W, ctas=k * sms, queue=queue), reps)
-    best = min(times, key=times.get)
-    return {"best_ctas": int(best), "times_ms": {str(k): v for k, v in times.items()}}
+    default = dict(ctas=3 * sms, packet=256, chunk=1, staging=0, occupancy=0)
+    space = [("ctas", [k * sms for k in (1, 2, 3, 4, 6, 8)]), ("packet", [256, 128, 64]), ("chunk", [1, 2, 4, 8, 16]),
+             ("staging", [0, 1]), ("occupancy", [0, 1] if W == 8 else [0])]
+    trials = {}
+
+    def timed(cfg):
+        key = tuple(sorted(cfg.items()))
+        if key not in trials:
+            trials[key] = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **cfg), reps)
+        return trials[key]
+
+    best, best_t = dict(default), timed(default)
+    for _ in range(rounds):
+        for name, values in space:
+            for v in values:
+                cand = dict(best, **{name: v})
+                t = timed(cand)
+                if t < best_t:
+                    best, best_t = cand, t
+    return {"best": best, "best_ms": best_t, "default": default, "default_ms": trials[tuple(sorted(default.items()))],
+            "trials": [{"config": dict(k), "ms": v} for k, v in trials.items()]}
+
+
+def tune_threshold(ctx, atms, W, cfg, thresholds=(0.0, 1e-4, 1e-3, 1e-2, 1.0, 1e30), bar_pct=0.5, reps=3):
+    """The IoD threshold of the batch: the fastest of ``thresholds`` whose J error
+    against the full-resolution solve (MIP 0 only) has a 99.9th percentile of at
+    most ``bar_pct`` % over every probe and wavelength of every atmosphere; if
+    none meets it, the most accurate one (threshold 0 leaves only the
+    always-average rule of Section 2.2)."""
+    queue = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ref = []
+    for a in atms:
+        a.build(max_mip=0)
+    items = [a.item() for a in atms]
+    api.batch_solve_config(ctx, items, W, queue=queue, **cfg)
+    ctx.check()
+    ref = [a.J.clone() for a in atms]
+    out = []
+    for thr in thresholds:
+        for a in atms:
+            a.iod = thr
+            a.build()
+        items = [a.item() for a in atms]
+        t = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **cfg), reps)
+        ctx.check()
+        errs = []
+        for a, r in zip(atms, ref):
+            mask = r > 0
+            errs.append((((a.J - r).abs() / r.clamp_min(1e-30))[mask] * 100.0).double().cpu().numpy())
+        e = np.concatenate(errs)
+        out.append({"iod": thr, "ms": t, "j_err_pct_p99.9": float(np.percentile(e, 99.9)),
+                    "j_err_pct_max": float(e.max())})
+    ok = [o for o in out if o["j_err_pct_p99.9"] <= bar_pct]
+    best = min(ok, key=lambda o: o["ms"]) if ok else min(out, key=lambda o: o["j_err_pct_p99.9"])
+    return {"bar": f"J error p99.9 <= {bar_pct}% vs the full-resolution solve", "trials": out,
+            "best_iod": best["iod"], "bar_met": bool(ok)}
 
 
 class Atmosphere:
@@ -71,13 +128,15 @@ class Atmosphere:
         self.mips = None
         self.build()
 
-    def build(self):
+    def build(self, max_mip=3):
         p = self.params
         api.synth_static_line(self.ctx, p["chi_c"], p["s_c"], p["s_l"], p["ratio"], p["dld"], p["dlam"],
                               eta=self.eta, chi=self.chi)
         self.grid = api.grid_build(self.ctx, self.spec["nx"], self.spec["nz"], self.eta, self.chi, out=self.grid)
-        self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, self.W, 3, self.iod, self.iod, 0.25,
-                                   out=self.mips)
+        if self.mips is not None and self.mips.max_mip != max_mip:
+            self.mips = None
+        self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, self.W, max_mip, self.iod, self.iod,
+                                   0.25, out=self.mips)
 
     def solve(self):
         api.formal_solve_hdda(self.ctx, self.grid, self.mips, self.dirs, self.w, J=self.J, band=DISTANCE_LIMITS)
@@ -99,7 +158,7 @@ class Atmosphere:
         return int(seg.item()) * self.W
 
 
-def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3):
+def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3, tune_iod=True):
     import synth
     ctx = api.Context(0)
     specs = synth.batch_specs(n_atm, scale=scale) if seed is None else synth.batch_specs(n_atm, seed=seed, scale=scale)
@@ -108,17 +167,18 @@ def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3):
     dense = [a.dense_seg_lambda() for a in atms]
     items = [a.item() for a in atms]
     tuned = tune_batch(ctx, items, W, reps=reps)
-    ctas = tuned["best_ctas"]
+    cfg = tuned["best"]
+    ctas = cfg["ctas"]
     queue = torch.zeros(1, dtype=torch.int32, device="cuda")
-
     # sequential: one launch per atmosphere (solve only), and the whole step
     t_seq = _time(lambda: [a.solve() for a in atms], reps)
-    t_pers = _time(lambda: api.batch_solve(ctx, items, W, ctas=ctas, queue=queue), reps)
+    t_pers = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **cfg), reps)
+    t_pers_default = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **tuned["default"]), reps)
 
     def whole_step():
         for a in atms:
             a.build()
-        api.batch_solve(ctx, items, W, ctas=ctas, queue=queue)
+        api.batch_solve_config(ctx, items, W, queue=queue, **cfg)
 
     t_step_eager = _time(whole_step, reps)
     # capture the whole step in a CUDA graph (the library calls enqueue on the capture stream)
@@ -135,7 +195,7 @@ def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3):
     ctx.set_stream(old)
     torch.cuda.current_stream().wait_stream(s)
     t_graph = _time(g.replay, reps)
-    done, start = api.batch_solve(ctx, items, W, ctas=ctas, queue=queue, timing=True)
+    done, start = api.batch_solve_config(ctx, items, W, queue=queue, timing=True, **cfg)
     ctx.check()
     per_atm_ms = ((done.cpu().numpy() - int(start.item())) / 1e6).tolist()
     total_dense = float(sum(dense))
@@ -147,13 +207,16 @@ def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3):
         "tuning": tuned,
         "sequential_solve_ms": t_seq,
         "persistent_solve_ms": t_pers,
+        "persistent_default_config_ms": t_pers_default,
         "persistent_speedup_vs_sequential": t_seq / t_pers,
+        "tuned_speedup_vs_default_config": t_pers_default / t_pers,
         "step_eager_ms": t_step_eager,
         "step_graph_ms": t_graph,
         "aggregate_seg_lambda_per_s": {"sequential": total_dense / (t_seq / 1e3),
                                        "persistent": total_dense / (t_pers / 1e3),
                                        "graph_step": total_dense / (t_graph / 1e3)},
         "per_atmosphere_done_ms": per_atm_ms,
+        "threshold_tuning": tune_threshold(ctx, atms, W, cfg, reps=reps) if tune_iod else None,
     }
 
 
@@ -161,9 +224,10 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--n-atm", type=int, default=24)
+    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
-    rep = batch_report(scale=args.scale, n_atm=args.n_atm)
+    rep = batch_report(scale=args.scale, n_atm=args.n_atm, reps=args.reps)
     s = json.dumps(rep)
     if args.out:
         with open(args.out, "w") as f:

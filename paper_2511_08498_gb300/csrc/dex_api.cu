@@ -915,7 +915,7 @@ int dex_formal_solve_velinterp(dex_ctx* ctx, int nx, int nz, int n_lambda, int W
 
 // Validate the batch descriptors and fill the launch parameters (no launch).
 static int fill_batch(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, dex::BatchParams& P,
-                      size_t& max_words)
+                      size_t& max_words, int parts = 1, size_t* max_blocks = nullptr)
 {
     if (n_atm < 1 || n_atm > DEX_MAX_BATCH_ATM)
         return fail(ctx, DEX_ERR_ARG, "n_atm must be in [1, %d], got %d", DEX_MAX_BATCH_ATM, n_atm);
@@ -963,18 +963,22 @@ static int fill_batch(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W
         A.dirs = it.dirs;
         A.weights = it.weights;
         A.J = it.J;
-        base += (long long)((it.n_lambda + W - 1) / W) * it.capacity;
+        base += (long long)((it.n_lambda + W - 1) / W) * it.capacity * parts;
         if ((size_t)A.n_words > max_words) max_words = (size_t)A.n_words;
+        if (max_blocks && (size_t)nb > *max_blocks) *max_blocks = (size_t)nb;
     }
     if (base > 0xffffffffLL) return fail(ctx, DEX_ERR_ARG, "too many work items");
     P.n_items = base;
+    P.parts = parts;
+    P.chunk = 1;
     return DEX_OK;
 }
 
 // Zero every J, then launch the persistent solve with the given work counter.
 static int batch_launch(dex_ctx* ctx, dex::BatchParams& P, const dex_batch_item* atms, int W, int ctas,
                         size_t max_words, unsigned int* queue, unsigned long long* done_ns,
-                        unsigned long long* start_ns)
+                        unsigned long long* start_ns, int packet = 256, bool info = false, size_t max_blocks = 0,
+                        bool occupancy = false)
 {
     if (int r = own_cell_required(ctx, "the batched solve")) return r;
     P.queue = queue;
@@ -992,7 +996,8 @@ static int batch_launch(dex_ctx* ctx, dex::BatchParams& P, const dex_batch_item*
                             ctx->stream);
     if (e == cudaSuccess && done_ns) e = cudaMemsetAsync(done_ns, 0, sizeof(unsigned long long) * P.n_atm, ctx->stream);
     if (e == cudaSuccess && start_ns) e = cudaMemsetAsync(start_ns, 0xff, sizeof(unsigned long long), ctx->stream);
-    if (e == cudaSuccess) e = dex::launch_batch_solve(ctx->stream, P, ctas, W, max_words);
+    const size_t smem = info ? sizeof(int) * max_blocks : sizeof(unsigned long long) * max_words;
+    if (e == cudaSuccess) e = dex::launch_batch_solve(ctx->stream, P, ctas, W, packet, info, occupancy, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch_solve launch");
     return ok(ctx);
 }
@@ -1008,6 +1013,36 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
     int r = fill_batch(ctx, n_atm, atms, W, *P, max_words);
     if (!r) r = bind(ctx);
     if (!r) r = batch_launch(ctx, *P, atms, W, ctas, max_words, queue, done_ns, start_ns);
+    delete P;
+    return r;
+}
+
+int dex_batch_solve_config(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, const dex_batch_config* cfg,
+                           unsigned int* queue, unsigned long long* done_ns, unsigned long long* start_ns)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (!cfg) return fail(ctx, DEX_ERR_ARG, "config required");
+    if (!queue) return fail(ctx, DEX_ERR_ARG, "queue (device scratch word) required");
+    if (cfg->packet != 256 && cfg->packet != 128 && cfg->packet != 64)
+        return fail(ctx, DEX_ERR_ARG, "packet must be 256, 128 or 64 probes, got %d", cfg->packet);
+    if (cfg->chunk < 1 || cfg->chunk > 64) return fail(ctx, DEX_ERR_ARG, "chunk must be in [1, 64], got %d", cfg->chunk);
+    if (cfg->staging != 0 && cfg->staging != 1) return fail(ctx, DEX_ERR_ARG, "staging must be 0 or 1");
+    if (cfg->occupancy != 0 && cfg->occupancy != 1) return fail(ctx, DEX_ERR_ARG, "occupancy must be 0 or 1");
+    if (cfg->occupancy == 1 && W != 8) return fail(ctx, DEX_ERR_ARG, "the 64-register budget is built for W = 8");
+    if (cfg->ctas < 0) return fail(ctx, DEX_ERR_ARG, "ctas must be >= 0");
+    dex::BatchParams* P = new (std::nothrow) dex::BatchParams();
+    if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
+    size_t max_words = 0, max_blocks = 0;
+    int r = fill_batch(ctx, n_atm, atms, W, *P, max_words, 256 / cfg->packet, &max_blocks);
+    if (!r && cfg->staging == 1 && max_blocks > (size_t)dex::kInfoMaxBlocks)
+        r = fail(ctx, DEX_ERR_ARG, "one-word-per-block staging needs grids of at most %d blocks", dex::kInfoMaxBlocks);
+    if (!r) {
+        P->chunk = cfg->chunk;
+        r = bind(ctx);
+    }
+    if (!r)
+        r = batch_launch(ctx, *P, atms, W, cfg->ctas, max_words, queue, done_ns, start_ns, cfg->packet,
+                         cfg->staging == 1, max_blocks, cfg->occupancy == 1);
     delete P;
     return r;
 }

@@ -38,6 +38,9 @@ struct MipParams {
     unsigned int* status;
 };
 
+// Grids of at most this many blocks stage the one-word-per-block table (32 KB).
+constexpr int kInfoMaxBlocks = 8192;
+
 struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
@@ -165,6 +168,8 @@ struct AtmDesc {
 struct BatchParams {
     int n_atm;
     long long n_items;
+    int parts;              // work items per active block and batch: 256 / probes per item
+    int chunk;              // work items claimed per queue increment
     unsigned int* queue;
     unsigned long long* done_ns;
     unsigned long long* start_ns;
@@ -172,7 +177,12 @@ struct BatchParams {
     AtmDesc atm[DEX_MAX_BATCH_ATM];
 };
 
-cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, size_t smem_words);
+// packet: probes per work item (256, 128 or 64); info: stage one word per block
+// (offset * 8 + state) instead of the packed state words; occupancy (W = 8): a
+// 64-register budget (four 256-thread CTAs per SM) instead of the compiler's;
+// smem_bytes: the largest table of the batch
+cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, int packet, bool info,
+                               bool occupancy, size_t smem_bytes);
 cudaError_t noalloc_scratch(unsigned int** out);
 
 int chain_length(int max_mip);

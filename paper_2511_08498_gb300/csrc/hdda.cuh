@@ -62,8 +62,6 @@ struct InfoLookup {
     __device__ __forceinline__ int offset_of(int k) const { return k >> 3; }
 };
 
-// Grids of at most this many blocks stage the one-word-per-block table (32 KB).
-constexpr int kInfoMaxBlocks = 8192;
 
 __device__ __forceinline__ int pack_block_info(int offset, int state) { return offset * 8 + state; }
 

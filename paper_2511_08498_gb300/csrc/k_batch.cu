@@ -1,10 +1,10 @@
 // Many independent atmospheres in one persistent launch.
 //
-// Work items are (atmosphere, wavelength batch, active block), numbered
-// atmosphere by atmosphere (item_base[a] + batch * capacity_a + rank).  A fixed
-// grid of CTAs pulls items from a device counter (the queue) until it runs dry;
-// each item is the same 256-probe block solve as k_solve_hdda_t (shared
-// trace_ray).  Consecutive items mostly share an atmosphere and batch, so the
+// Work items are (atmosphere, wavelength batch, active block, part of the
+// block), numbered atmosphere by atmosphere (item_base[a] + (batch * capacity_a
+// + rank) * parts + part).  A fixed grid of CTAs pulls `chunk` items at a time
+// from a device counter (the queue) until it runs dry; each item is the block
+// solve of k_solve_hdda_t (shared trace_ray) over 256 / parts of its probes.  Consecutive items mostly share an atmosphere and batch, so the
 // staged block states and quadrature are reused, and the L2 working set stays
 // one atmosphere batch wide.  Per-atmosphere completion times (globaltimer, ns)
 // are recorded when requested.
@@ -44,13 +44,24 @@ struct StaticRec {
     }
 };
 
-template <int W>
-__global__ void __launch_bounds__(256) k_batch_solve(const BatchParams P)
+// kMinCtas: CTAs per SM the register budget is sized for (1: the compiler's
+// choice, 97 registers at W = 8; 1024 / NT: 64 registers, four 256-thread CTAs
+// of residency, with some spilling).
+// NT threads per CTA = probes per work item (a 16 x (NT / 16) part of a block,
+// warps on 8 x 4 tiles as in k_solve_hdda_t); a CTA claims `chunk` consecutive
+// items per queue increment.  kInfo: the block table is staged as one word per
+// block (offset * 8 + state); otherwise the packed 3-bit state words.  Every
+// probe accumulates J over all directions in its thread, in the order of the
+// single-grid solve, so results do not depend on these choices.
+template <int W, int NT, bool kInfo, int kMinCtas>
+__global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams P)
 {
-    extern __shared__ unsigned long long s_words[];
-    __shared__ float s_J[W][256];
+    extern __shared__ unsigned long long s_dyn[];
+    __shared__ float s_J[W][NT];
     __shared__ float s_dx[DEX_MAX_DIRS], s_dz[DEX_MAX_DIRS], s_w[DEX_MAX_DIRS];
     __shared__ unsigned int s_item;
+    constexpr int kParts = 256 / NT;
+    int* s_info = reinterpret_cast<int*>(s_dyn);
     const int tid = threadIdx.x;
     int cur_atm = -1, cur_batch = -1;
     unsigned int nseg_unused = 0;
@@ -58,75 +69,118 @@ __global__ void __launch_bounds__(256) k_batch_solve(const BatchParams P)
     if (P.start_ns != nullptr && tid == 0) atomicMin(P.start_ns, global_ns());
 
     for (;;) {
-        __syncthreads();  // every thread is done with the previous item's shared data
-        if (tid == 0) s_item = atomicAdd(P.queue, 1u);
+        __syncthreads();  // every thread is done with the previous claim
+        if (tid == 0) s_item = atomicAdd(P.queue, (unsigned int)P.chunk);
         __syncthreads();
-        const unsigned int item = s_item;
-        if ((long long)item >= P.n_items) break;
-        int a = 0;
-        while (a + 1 < P.n_atm && (long long)item >= P.atm[a + 1].item_base) ++a;
-        const AtmDesc& A = P.atm[a];
-        const long long local = (long long)item - A.item_base;
-        const int b = (int)(local / A.cap_active), r = (int)(local % A.cap_active);
-        if (r >= *A.n_active) continue;
-        if (a != cur_atm || b != cur_batch) {
-            for (int q = tid; q < A.n_words; q += blockDim.x) s_words[q] = A.words[(size_t)b * A.n_words + q];
-            if (a != cur_atm)
-                for (int q = tid; q < A.n_dir; q += blockDim.x) {
-                    s_dx[q] = A.dirs[2 * q];
-                    s_dz[q] = A.dirs[2 * q + 1];
-                    s_w[q] = A.weights[q];
+        const unsigned int first = s_item;
+        if ((long long)first >= P.n_items) break;
+        for (int c = 0; c < P.chunk; ++c) {
+            const long long item = (long long)first + c;
+            if (item >= P.n_items) break;
+            int a = 0;
+            while (a + 1 < P.n_atm && item >= P.atm[a + 1].item_base) ++a;
+            const AtmDesc& A = P.atm[a];
+            const long long local = item - A.item_base;
+            const long long unit = local / kParts;
+            const int part = (int)(local % kParts);
+            const int b = (int)(unit / A.cap_active), r = (int)(unit % A.cap_active);
+            if (r >= *A.n_active) continue;
+            __syncthreads();  // every thread is done with the previous item's shared data
+            if (a != cur_atm || b != cur_batch) {
+                if constexpr (kInfo) {
+                    const int nb = A.nbx * A.nbz;
+                    const unsigned long long* wb = A.words + (size_t)b * A.n_words;
+                    for (int q = tid; q < nb; q += NT) s_info[q] = pack_block_info(A.block_offset[q], block_state(wb, q));
+                } else {
+                    for (int q = tid; q < A.n_words; q += NT) s_dyn[q] = A.words[(size_t)b * A.n_words + q];
                 }
-            cur_atm = a;
-            cur_batch = b;
-        }
+                if (a != cur_atm)
+                    for (int q = tid; q < A.n_dir; q += NT) {
+                        s_dx[q] = A.dirs[2 * q];
+                        s_dz[q] = A.dirs[2 * q + 1];
+                        s_w[q] = A.weights[q];
+                    }
+                cur_atm = a;
+                cur_batch = b;
+            }
 #pragma unroll
-        for (int w = 0; w < W; ++w) s_J[w][tid] = 0.0f;
-        __syncthreads();
-
-        const int blk0 = A.active[r];
-        const int bx0 = blk0 % A.nbx, bz0 = blk0 / A.nbx;
-        // warp w: an 8 x 4 tile of the block (the probe order of k_solve_hdda_t)
-        const int i = bx0 * DEX_BLOCK + ((tid >> 5) & 1) * 8 + (tid & 7);
-        const int j = bz0 * DEX_BLOCK + (tid >> 6) * 4 + ((tid & 31) >> 3);
-        const int state0 = block_state(s_words, blk0) - 1;
-        if (state0 < 0) {
-            capped = true;
-            continue;
-        }
-        Geo G;
-        G.nx = A.nx;
-        G.nz = A.nz;
-        G.nbx = A.nbx;
-        G.nbz = A.nbz;
-        G.chain = A.chain;
-        G.cap_active = A.cap_active;
-        G.batch_base = A.bricks + (size_t)b * A.cap_active * A.chain * (2 * W);
-        set_bands(G, A.n_band, A.band);
-        const int mip0 = min(state0, distance_cap(G, 0.0f));
-        typename StaticRec<W>::Params M{};
-        for (int k = 0; k < A.n_dir; ++k) {
-            float I[W], T[W];
-#pragma unroll
-            for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
-            trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
-                                               WordLookup{s_words, A.block_offset}, I, T, nseg_unused, capped);
-            const float wk = s_w[k];
-#pragma unroll
-            for (int w = 0; w < W; ++w) s_J[w][tid] = fmaf(wk, fmaf(T[w], A.i_bc, I[w]), s_J[w][tid]);
-        }
-        const long long n_cells = (long long)A.nx * A.nz;
-#pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const int l = b * W + w;
-            if (l < A.n_lambda) A.J[(size_t)l * n_cells + (size_t)j * A.nx + i] = s_J[w][tid];
-        }
-        if (P.done_ns != nullptr) {
+            for (int w = 0; w < W; ++w) s_J[w][tid] = 0.0f;
             __syncthreads();
-            if (tid == 0) atomicMax(P.done_ns + a, global_ns());
+
+            const int blk0 = A.active[r];
+            const int bx0 = blk0 % A.nbx, bz0 = blk0 / A.nbx;
+            const int wrp = tid >> 5;
+            const int i = bx0 * DEX_BLOCK + (wrp & 1) * 8 + (tid & 7);
+            const int j = bz0 * DEX_BLOCK + part * (DEX_BLOCK / kParts) + (wrp >> 1) * 4 + ((tid & 31) >> 3);
+            const int state0 = (kInfo ? (s_info[blk0] & 7) : block_state(s_dyn, blk0)) - 1;
+            if (state0 < 0) {
+                capped = true;
+                continue;
+            }
+            Geo G;
+            G.nx = A.nx;
+            G.nz = A.nz;
+            G.nbx = A.nbx;
+            G.nbz = A.nbz;
+            G.chain = A.chain;
+            G.cap_active = A.cap_active;
+            G.batch_base = A.bricks + (size_t)b * A.cap_active * A.chain * (2 * W);
+            set_bands(G, A.n_band, A.band);
+            const int mip0 = min(state0, distance_cap(G, 0.0f));
+            typename StaticRec<W>::Params M{};
+            for (int k = 0; k < A.n_dir; ++k) {
+                float I[W], T[W];
+#pragma unroll
+                for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
+                if constexpr (kInfo)
+                    trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
+                                                       InfoLookup{s_info}, I, T, nseg_unused, capped);
+                else
+                    trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
+                                                       WordLookup{s_dyn, A.block_offset}, I, T, nseg_unused, capped);
+                const float wk = s_w[k];
+#pragma unroll
+                for (int w = 0; w < W; ++w) s_J[w][tid] = fmaf(wk, fmaf(T[w], A.i_bc, I[w]), s_J[w][tid]);
+            }
+            const long long n_cells = (long long)A.nx * A.nz;
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                const int l = b * W + w;
+                if (l < A.n_lambda) A.J[(size_t)l * n_cells + (size_t)j * A.nx + i] = s_J[w][tid];
+            }
+            if (P.done_ns != nullptr) {
+                __syncthreads();
+                if (tid == 0) atomicMax(P.done_ns + a, global_ns());
+            }
         }
     }
     if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
+}
+
+template <int W, int NT, bool kInfo, int kMinCtas>
+cudaError_t launch_batch_t(cudaStream_t s, const BatchParams& P, int ctas, size_t smem)
+{
+    auto kernel = k_batch_solve<W, NT, kInfo, kMinCtas>;
+    if (smem > 16 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kernel<<<(unsigned)ctas, NT, smem, s>>>(P);
+    return cudaSuccess;
+}
+
+template <int W, bool kOcc>
+cudaError_t launch_batch_w(cudaStream_t s, const BatchParams& P, int ctas, int packet, bool info, size_t smem)
+{
+    switch (packet * 2 + (info ? 1 : 0)) {
+        case 256 * 2: return launch_batch_t<W, 256, false, kOcc ? 4 : 1>(s, P, ctas, smem);
+        case 256 * 2 + 1: return launch_batch_t<W, 256, true, kOcc ? 4 : 1>(s, P, ctas, smem);
+        case 128 * 2: return launch_batch_t<W, 128, false, kOcc ? 8 : 1>(s, P, ctas, smem);
+        case 128 * 2 + 1: return launch_batch_t<W, 128, true, kOcc ? 8 : 1>(s, P, ctas, smem);
+        case 64 * 2: return launch_batch_t<W, 64, false, kOcc ? 16 : 1>(s, P, ctas, smem);
+        case 64 * 2 + 1: return launch_batch_t<W, 64, true, kOcc ? 16 : 1>(s, P, ctas, smem);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -145,24 +199,20 @@ cudaError_t noalloc_scratch(unsigned int** out)
     return cudaSuccess;
 }
 
-cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, size_t smem_words)
+cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, int packet, bool info,
+                               bool occupancy, size_t smem_bytes)
 {
     cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess || P.n_items == 0) return e;
-    const size_t smem = sizeof(unsigned long long) * smem_words;
+    if (occupancy && W != 8) return cudaErrorInvalidValue;
     switch (W) {
-#define DEX_LAUNCH(WW)                                                                                  \
-    case WW:                                                                                            \
-        if (smem > 16 * 1024)                                                                           \
-            e = cudaFuncSetAttribute(k_batch_solve<WW>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                     (int)smem);                                                        \
-        if (e == cudaSuccess) k_batch_solve<WW><<<(unsigned)ctas, 256, smem, s>>>(P);                   \
-        break;
-        DEX_LAUNCH(1)
-        DEX_LAUNCH(2)
-        DEX_LAUNCH(4)
-        DEX_LAUNCH(8)
-#undef DEX_LAUNCH
+        case 1: e = launch_batch_w<1, false>(s, P, ctas, packet, info, smem_bytes); break;
+        case 2: e = launch_batch_w<2, false>(s, P, ctas, packet, info, smem_bytes); break;
+        case 4: e = launch_batch_w<4, false>(s, P, ctas, packet, info, smem_bytes); break;
+        case 8:
+            e = occupancy ? launch_batch_w<8, true>(s, P, ctas, packet, info, smem_bytes)
+                          : launch_batch_w<8, false>(s, P, ctas, packet, info, smem_bytes);
+            break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

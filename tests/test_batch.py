@@ -50,3 +50,42 @@ def test_batch_equals_per_atmosphere(ctas):
         assert torch.equal(a["J"], r)
     d = done.cpu().numpy()
     assert (d > 0).all() and (d >= int(start.item())).all()
+
+
+# every knob of the batched launch the autotuner sweeps: probes per work item,
+# items per queue claim, block-table staging, register budget, grid size
+CONFIGS = [dict(ctas=0, packet=128, chunk=1, staging=0, occupancy=0),
+           dict(ctas=5, packet=64, chunk=3, staging=1, occupancy=0),
+           dict(ctas=0, packet=256, chunk=8, staging=1, occupancy=1),
+           dict(ctas=304, packet=64, chunk=2, staging=0, occupancy=1),
+           dict(ctas=1, packet=128, chunk=64, staging=1, occupancy=1)]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_every_configuration_equals_per_atmosphere(cfg):
+    from paper_2511_08498_gb300 import api
+    ctx = api.Context(0)
+    atms = build_atmospheres(ctx, SPECS)
+    refs = []
+    for a in atms:
+        J, _, _ = api.formal_solve_hdda(ctx, a["grid"], a["mips"], a["dirs"], a["w"], band=a["band"])
+        refs.append(J.clone())
+    items = [api.batch_item(a["grid"], a["mips"], a["dirs_dev"], a["w_dev"], a["J"], band=a["band"]) for a in atms]
+    for a in atms:
+        a["J"].fill_(-1.0)
+    done, start = api.batch_solve_config(ctx, items, 8, timing=True, **cfg)
+    ctx.check()
+    for a, r in zip(atms, refs):
+        assert torch.equal(a["J"], r), cfg
+    d = done.cpu().numpy()
+    assert (d > 0).all() and (d >= int(start.item())).all()
+
+
+def test_configuration_is_checked():
+    from paper_2511_08498_gb300 import api
+    ctx = api.Context(0)
+    atms = build_atmospheres(ctx, SPECS[:1])
+    items = [api.batch_item(a["grid"], a["mips"], a["dirs_dev"], a["w_dev"], a["J"], band=a["band"]) for a in atms]
+    for bad in (dict(packet=96), dict(chunk=0), dict(chunk=65), dict(staging=2), dict(occupancy=3)):
+        with pytest.raises(api.DexError):
+            api.batch_solve_config(ctx, items, 8, **bad)
