@@ -425,7 +425,13 @@ def native(args):
                      "peak_ex2_per_sm_clk": ex2_rate / n_sm / (sm_clock_mhz * 1e6),
                      "kernel_ms": hdda_s * 1e3, "executed_seg_lambda": exec_seg_lambda,
                      "hbm_algorithmic_gbs": exec_seg_lambda * 8 / hdda_s / 1e9,
-                     "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "peak_source": peak_src},
+                     "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "peak_source": peak_src,
+                     "hbm_binds": False,
+                     "hbm_note": "HBM does not bind: the 8 B per update come from L1/L2 (the algorithmic GB/s "
+                                 "exceeds the HBM peak); DRAM sees about one read of each wavelength batch's "
+                                 "bricks plus J per launch ('traffic').  The ceiling is instruction issue, "
+                                 "reported against the 2^x rate since one exponential per update is the "
+                                 "only unavoidable special-function operation"},
         "plain": {"value": dense_seg_lambda / plain_s, "ms_per_step": plain_s * 1e3,
                   "kernel_ms": plain_kern_s * 1e3, "kernel_updates_per_s": plain_achieved * 1e9,
                   "kernel_frac_of_sfu_peak": plain_achieved / sfu_peak,
