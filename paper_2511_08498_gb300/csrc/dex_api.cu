@@ -470,6 +470,7 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
         }
         P.n_band = n_band;
     }
+    dex::pad_bands(P.n_band, P.band);
     if (int r = fill_quadrature(ctx, n_dir, dirs, weights, P.quad)) return r;
     if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
         return fail(ctx, DEX_ERR_ARG, "null buffer");
@@ -829,6 +830,7 @@ static int solve_cav(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_
         }
         P.n_band = n_band;
     }
+    dex::pad_bands(P.n_band, P.band);
     if (!bricks || !state_words || !block_offset || !active || !n_active || !J)
         return fail(ctx, DEX_ERR_ARG, "null buffer");
     if (!aligned(bricks, 16)) return fail(ctx, DEX_ERR_ARG, "bricks must be 16-byte aligned");
@@ -953,6 +955,7 @@ static int fill_batch(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W
         for (int q = 0; q < 4; ++q) A.band[q] = it.band[q];
         for (int q = 1; q < (A.n_band > 0 ? A.n_band : 0); ++q)
             if (!(A.band[q] >= A.band[q - 1])) return fail(ctx, DEX_ERR_ARG, "atmosphere %d: bad thresholds", a);
+        dex::pad_bands(A.n_band, A.band);
         A.i_bc = it.i_bc;
         A.item_base = base;
         A.bricks = it.bricks;

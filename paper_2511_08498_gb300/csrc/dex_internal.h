@@ -41,9 +41,20 @@ struct MipParams {
 // Grids of at most this many blocks stage the one-word-per-block table (32 KB).
 constexpr int kInfoMaxBlocks = 8192;
 
+// Distance thresholds of levels 1..4 padded to four, as the traversal compares
+// them (the number of thresholds band[m-1] <= t is the highest level allowed):
+// +inf for the levels beyond the n_band given (never reached), 0 for all four
+// when there is no limit (n_band < 0: every level allowed from t = 0).
+inline void pad_bands(int n_band, float* band)
+{
+    for (int q = 0; q < 4; ++q)
+        band[q] = n_band < 0 ? 0.0f : (q < n_band ? band[q] : __builtin_huge_valf());
+}
+
 struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
+                     // (band padded to four by pad_bands)
     int traversal;   // DEX_TRAVERSAL_PER_BATCH or DEX_TRAVERSAL_SHARED (static model, W = 8)
     int exclude_own; // leave out each probe's own-voxel emission (static model, W = 8, float32)
     float band[4];

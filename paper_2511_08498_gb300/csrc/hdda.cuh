@@ -12,18 +12,19 @@ __host__ __device__ constexpr int level_offset(int m) { return 341 - (341 >> (2 
 // Geometry of one sparse grid as the traversal needs it.
 struct Geo {
     int nx, nz, nbx, nbz, chain, cap_active;
-    const float* batch_base;   // bricks of the wavelength batch being solved
-    float band[4];             // distance thresholds, padded (see set_bands)
+    int x_lo, x_hi, z_lo, z_hi;  // cell faces bounding the non-empty blocks
+    const float* batch_base;     // bricks of the wavelength batch being solved
+    float band[4];               // distance thresholds, padded (pad_bands)
 };
 
-// Distance thresholds of levels 1..4 padded to four: +inf for the levels beyond
-// the n_band given (never reached), 0 for all four when there is no limit
-// (n_band < 0: every level allowed from t = 0).
-__device__ __forceinline__ void set_bands(Geo& G, int n_band, const float* band)
+// Rays end where they leave this box: beyond it every block is empty and adds
+// nothing to I or T.  The whole grid, where the box is not known.
+__device__ __forceinline__ void set_box_full(Geo& G)
 {
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        G.band[q] = n_band < 0 ? 0.0f : (q < n_band ? band[q] : __int_as_float(0x7f800000));
+    G.x_lo = 0;
+    G.x_hi = G.nx;
+    G.z_lo = 0;
+    G.z_hi = G.nz;
 }
 
 // Highest level a block first entered at ray parameter t >= 0 may use: the
@@ -65,29 +66,44 @@ struct InfoLookup {
 
 __device__ __forceinline__ int pack_block_info(int offset, int state) { return offset * 8 + state; }
 
+namespace {
+// A record of zeros (any static record format up to 32 floats).  Integrating it
+// changes nothing: tau = 0, so 2^x = 1, 1 - e^{-tau} = 0, I += T * 0 and T *= 1.
+// Rays of models with kZeroNoop read it in empty blocks instead of branching
+// around the update.
+__device__ __align__(32) float g_zero_record[32] = {0.0f};
+}  // namespace
+
 // Voxel models: Model::kStride floats per voxel record, Model::kPerBatch whether
 // records differ per wavelength batch, Model::kEarlyLoad whether the record is
-// loaded at the top of each step, Model::Voxel / load / integrate the
-// per-segment update of the W wavelengths of batch b along propagation (wx, wz).
+// loaded at the top of each step, Model::kZeroNoop whether a record of zeros
+// integrates to no change, Model::Voxel / load / integrate the per-segment
+// update of the W wavelengths of batch b along propagation (wx, wz).
 //
 // One ray from the centre of cell (i, j) (in active block a0 = (bx0, bz0), whose
 // level is mip0) along d = (dx, dz): accumulates I and T (initialised by the
 // caller) over the traversal; L looks up the batch's block states and offsets.
 // EXT: the emission of the probe's own voxel (the first segment) is left out.
+//
+// Each step integrates the voxel it leaves, then steps to the next voxel of the
+// same level; only a step that leaves the block (one divergent branch) looks up
+// the next block.  A ray's block indices change monotonically and it takes at
+// most 2 * 16 steps in a block, so the grid bounds check also bounds the loop.
 template <int W, bool COUNT, class Model, class Lookup, bool EXT = false>
 __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Params& M, int b, int i, int j,
                                           int bx0, int bz0, int a0, int mip0, float dx, float dz,
                                           const Lookup& L, float* I, float* T, unsigned int& nseg, bool& capped)
 {
     constexpr int REC = Model::kStride;
+    constexpr bool kZero = Model::kZeroNoop;
     const float* __restrict__ batch_base = G.batch_base;
-    const int cap = 2 * (G.nx + G.nz) + 64;
     const float ox = (float)i + 0.5f, oz = (float)j + 0.5f;
     const bool negx = dx < 0.0f, negz = dz < 0.0f;
     const int sx = negx ? -1 : 1, sz = negz ? -1 : 1;
     const AxisParam ax = axis_param(dx), az = axis_param(dz);
-    const float Ex = negx ? (float)(-i) - 0.5f : (float)(G.nx - i) - 0.5f;
-    const float Ez = negz ? (float)(-j) - 0.5f : (float)(G.nz - j) - 0.5f;
+    // exit plane offsets: the faces of the box around the non-empty blocks
+    const float Ex = (float)((negx ? G.x_lo : G.x_hi) - i) - 0.5f;
+    const float Ez = (float)((negz ? G.z_lo : G.z_hi) - j) - 0.5f;
     const float t2 = fminf(Ex * ax.ih, Ez * az.ih);
 
     // tracer state: level, voxel size, block, block-local voxel, far-face plane offsets
@@ -101,13 +117,14 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
     float th_prev = 0.0f, tl_prev = 0.0f;
     typename Model::Voxel cur;
 
-    // unrolled four times: -3.6% on the 1024^2 benchmark solve (twice: -1.8%; bit-identical)
+    // unrolled four times (twice and eight times measured slower on the 1024^2
+    // benchmark solve)
 #pragma unroll 4
     for (int it = 0;; ++it) {
         // models with kEarlyLoad issue the current voxel's record before the
         // stepping and crossing bookkeeping, which then hides its latency
         if constexpr (Model::kEarlyLoad) {
-            if (mip >= 0) cur = Model::load(rp);
+            if (kZero || mip >= 0) cur = Model::load(rp);
         }
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
@@ -117,84 +134,81 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
         const bool last = th >= t2;
         const int cur_mip = mip;
         const float* cur_rp = rp;
-        if (!last) {
-            if (it >= cap) { capped = true; break; }
-            const float fv = fvox;
-            bool cross;
-            if (on_x) {
-                lx += sx;
-                Px += negx ? -fv : fv;
-                rp += negx ? -REC : REC;
-                cross = (unsigned)lx >= (unsigned)side;
-            } else {
-                lz += sz;
-                Pz += negz ? -fv : fv;
-                rp += negz ? -side * REC : side * REC;
-                cross = (unsigned)lz >= (unsigned)side;
-            }
-            // early termination, checked where the ray enters another block: once every
-            // transmission has underflowed to exactly zero the rest of the ray adds
-            // exact zeros, so stopping leaves I and T bit-identical
-            if (cross && all_opaque<W>(T)) break;
-            if (cross) {  // entered another block
-                const int bxn = bxc + (on_x ? sx : 0), bzn = bzc + (on_x ? 0 : sz);
-                if ((unsigned)bxn >= (unsigned)G.nbx || (unsigned)bzn >= (unsigned)G.nbz) {
-                    capped = true;
-                    break;
-                }
-                const int key = L.key(bzn * G.nbx + bxn);
-                const int st = L.state(key) - 1;
-                const int mip_new = st < 0 ? -1 : min(st, distance_cap(G, th));
-                if (mip_new == mip) {
-                    if (on_x) lx = negx ? side - 1 : 0;
-                    else lz = negz ? side - 1 : 0;
-                } else {
-                    // MIP-0 cell entered: exact on the stepped axis, from p(t) on the
-                    // other one, clamped to the voxel just left
-                    const int vox_old = vox;
-                    int m0x, m0z;
-                    if (on_x) {
-                        m0x = bxn * DEX_BLOCK + (negx ? DEX_BLOCK - 1 : 0);
-                        const int lo = bzc * DEX_BLOCK + lz * vox_old;
-                        m0z = min(max(__float2int_rd(fmaf(th, dz, oz)), lo), lo + vox_old - 1);
-                    } else {
-                        m0z = bzn * DEX_BLOCK + (negz ? DEX_BLOCK - 1 : 0);
-                        const int lo = bxc * DEX_BLOCK + lx * vox_old;
-                        m0x = min(max(__float2int_rd(fmaf(th, dx, ox)), lo), lo + vox_old - 1);
-                    }
-                    mip = mip_new;
-                    const int shift = mip >= 0 ? mip : 4;
-                    vox = 1 << shift;
-                    fvox = (float)vox;
-                    side = DEX_BLOCK >> shift;
-                    lx = (m0x - bxn * DEX_BLOCK) >> shift;
-                    lz = (m0z - bzn * DEX_BLOCK) >> shift;
-                    Px = (float)(bxn * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
-                    Pz = (float)(bzn * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
-                }
-                bxc = bxn;
-                bzc = bzn;
-                if (mip >= 0) {
-                    const int a = L.offset_of(key);
-                    rp = batch_base + ((size_t)a * G.chain + level_offset(mip) + lz * side + lx) * REC;
-                }
-            }
+        // step to the next voxel of this level (not used once last)
+        bool cross;
+        if (on_x) {
+            lx += sx;
+            Px += negx ? -fvox : fvox;
+            rp += negx ? -REC : REC;
+            cross = (unsigned)lx >= (unsigned)side;
+        } else {
+            lz += sz;
+            Pz += negz ? -fvox : fvox;
+            rp += negz ? -side * REC : side * REC;
+            cross = (unsigned)lz >= (unsigned)side;
         }
-        if (cur_mip >= 0) {
+        // integrate the voxel left (in empty blocks: the zero record, or nothing)
+        if (kZero || cur_mip >= 0) {
             if constexpr (!Model::kEarlyLoad) cur = Model::load(cur_rp);
-            const float nl2 = len * kNegLog2e;
-            Model::integrate(M, cur, b, -dx, -dz, nl2, I, T);
+            Model::integrate(M, cur, b, -dx, -dz, len * kNegLog2e, I, T);
             if constexpr (EXT) {
                 if (it == 0) {
 #pragma unroll
                     for (int w = 0; w < W; ++w) I[w] = 0.0f;
                 }
             }
-            if (COUNT) nseg += (th > th_prev);
+            if (COUNT) nseg += (cur_mip >= 0) & (th > th_prev);
         }
         if (last) break;
         th_prev = th;
         tl_prev = tl;
+        if (cross) {  // entered another block
+            // early termination: once every transmission has underflowed to exactly
+            // zero the rest of the ray adds exact zeros, so stopping leaves I and T
+            // bit-identical
+            if (all_opaque<W>(T)) break;
+            if (on_x) bxc += sx;
+            else bzc += sz;
+            if ((unsigned)bxc >= (unsigned)G.nbx || (unsigned)bzc >= (unsigned)G.nbz) {
+                capped = true;
+                break;
+            }
+            const int key = L.key(bzc * G.nbx + bxc);
+            const int st = L.state(key) - 1;
+            const int mip_new = st < 0 ? -1 : min(st, distance_cap(G, th));
+            if (mip_new == mip) {
+                if (on_x) lx = negx ? side - 1 : 0;
+                else lz = negz ? side - 1 : 0;
+            } else {
+                // MIP-0 cell entered: exact on the stepped axis, from p(t) on the
+                // other one, clamped to the voxel just left (the block index on that
+                // axis is unchanged)
+                const int vox_old = vox;
+                int m0x, m0z;
+                if (on_x) {
+                    m0x = bxc * DEX_BLOCK + (negx ? DEX_BLOCK - 1 : 0);
+                    const int lo = bzc * DEX_BLOCK + lz * vox_old;
+                    m0z = min(max(__float2int_rd(fmaf(th, dz, oz)), lo), lo + vox_old - 1);
+                } else {
+                    m0z = bzc * DEX_BLOCK + (negz ? DEX_BLOCK - 1 : 0);
+                    const int lo = bxc * DEX_BLOCK + lx * vox_old;
+                    m0x = min(max(__float2int_rd(fmaf(th, dx, ox)), lo), lo + vox_old - 1);
+                }
+                mip = mip_new;
+                const int shift = mip >= 0 ? mip : 4;
+                vox = 1 << shift;
+                fvox = (float)vox;
+                side = DEX_BLOCK >> shift;
+                lx = (m0x - bxc * DEX_BLOCK) >> shift;
+                lz = (m0z - bzc * DEX_BLOCK) >> shift;
+                Px = (float)(bxc * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
+                Pz = (float)(bzc * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
+            }
+            if (mip >= 0)
+                rp = batch_base + ((size_t)L.offset_of(key) * G.chain + level_offset(mip) + lz * side + lx) * REC;
+            else if (kZero)
+                rp = g_zero_record;
+        }
     }
 }
 
@@ -220,6 +234,32 @@ __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const H
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) s_J[w][tid] = 0.0f;
+    // box around the non-empty (active) blocks, in block units
+    __shared__ int s_box[4];
+    if (tid < 4) s_box[tid] = (tid & 1) ? -1 : 0x7fffffff;
+    __syncthreads();
+    {
+        int xlo = 0x7fffffff, xhi = -1, zlo = 0x7fffffff, zhi = -1;
+        const int na = *P.n_active;
+        for (int q = tid; q < na; q += blockDim.x) {
+            const int blk = P.active[q];
+            const int bz = blk / P.nbx, bx = blk - bz * P.nbx;
+            xlo = min(xlo, bx);
+            xhi = max(xhi, bx);
+            zlo = min(zlo, bz);
+            zhi = max(zhi, bz);
+        }
+        xlo = __reduce_min_sync(0xffffffffu, xlo);
+        xhi = __reduce_max_sync(0xffffffffu, xhi);
+        zlo = __reduce_min_sync(0xffffffffu, zlo);
+        zhi = __reduce_max_sync(0xffffffffu, zhi);
+        if ((tid & 31) == 0) {
+            atomicMin(&s_box[0], xlo);
+            atomicMax(&s_box[1], xhi);
+            atomicMin(&s_box[2], zlo);
+            atomicMax(&s_box[3], zhi);
+        }
+    }
     __syncthreads();
 
     const int blk0 = P.active[a0];
@@ -243,7 +283,12 @@ __global__ void __launch_bounds__(256, Model::kMinBlocks) k_solve_hdda_t(const H
     G.chain = P.chain;
     G.cap_active = P.cap_active;
     G.batch_base = P.bricks + (Model::kPerBatch ? (size_t)b * P.cap_active * P.chain * Model::kStride : (size_t)0);
-    set_bands(G, P.n_band, P.band);
+    G.x_lo = s_box[0] * DEX_BLOCK;
+    G.x_hi = (s_box[1] + 1) * DEX_BLOCK;
+    G.z_lo = s_box[2] * DEX_BLOCK;
+    G.z_hi = (s_box[3] + 1) * DEX_BLOCK;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) G.band[q] = P.band[q];
     const int mip0 = min(state0, distance_cap(G, 0.0f));
     unsigned int nseg = 0;
     bool capped = false;

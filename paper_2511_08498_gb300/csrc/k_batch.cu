@@ -32,6 +32,7 @@ template <int W>
 struct StaticRec {
     static constexpr int kStride = 2 * W;
     static constexpr bool kEarlyLoad = true;  // as the float32 static model of the single-grid solve
+    static constexpr bool kZeroNoop = true;
     struct Params {
         int unused;
     };
@@ -125,7 +126,9 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams 
             G.chain = A.chain;
             G.cap_active = A.cap_active;
             G.batch_base = A.bricks + (size_t)b * A.cap_active * A.chain * (2 * W);
-            set_bands(G, A.n_band, A.band);
+            set_box_full(G);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) G.band[q] = A.band[q];
             const int mip0 = min(state0, distance_cap(G, 0.0f));
             typename StaticRec<W>::Params M{};
             for (int k = 0; k < A.n_dir; ++k) {

@@ -61,6 +61,7 @@ struct CavMlpModel {
     static constexpr bool kPerBatch = false;
     static constexpr int kMinBlocks = 1;  // the network's 64 hidden values stay in registers
     static constexpr bool kEarlyLoad = false;
+    static constexpr bool kZeroNoop = false;  // profile parameters of zero are not a no-op
     using Params = CavMlpParams;
     struct Voxel {
         float p[kCavStride];
@@ -99,6 +100,7 @@ struct CavModel {
     static constexpr bool kPerBatch = false;
     static constexpr int kMinBlocks = 4;
     static constexpr bool kEarlyLoad = false;
+    static constexpr bool kZeroNoop = false;  // profile parameters of zero are not a no-op
     using Params = CavParams;
     struct Voxel {
         float p[kCavStride];

@@ -19,8 +19,10 @@
 // Plane parameters are two-float sums (see AxisParam) and t never decreases: a
 // plane found behind the ray (rounding after a re-initialisation) yields a
 // zero-length step.  These replace the paper's two nudges (advancing t by 1e-2
-// voxel on entering empty space, forcing t_h > t) with exact bookkeeping.  Every
-// ray also has a step cap; exceeding it sets DEX_ERR_TRAVERSAL_CAP.
+// voxel on entering empty space, forcing t_h > t) with exact bookkeeping.  A ray
+// ends where it leaves the box around the non-empty blocks (nothing beyond it
+// adds to I or T); a ray that would step out of the grid before that sets
+// DEX_ERR_TRAVERSAL_CAP.
 #include "hdda.cuh"
 
 namespace dex {
@@ -37,6 +39,7 @@ struct StaticModel {
     // record loaded at the top of each step: -3.3% (float32) on the 1024^2 benchmark
     // solve; +5% with the bfloat16 / float16 unpacking (register pressure)
     static constexpr bool kEarlyLoad = ST == kStoreF32;
+    static constexpr bool kZeroNoop = true;  // zero records integrate to no change
     struct Params {
         int unused;
     };

@@ -144,6 +144,14 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
 #pragma unroll
             for (int q = 0; q < NB; ++q) pos |= (th > th0[q] ? 1u : 0u) << q;
         }
+        // integrate the voxels that ended on this plane (records loaded at the top)
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            if ((ends >> q) & 1u) {
+                segments<8>(rec[q].S, rec[q].chi, nl2[q], I + 8 * q, T + 8 * q);
+                if (COUNT) nseg += (pos >> q) & 1u;
+            }
+        }
         if (!last) {
             if (it >= cap) { capped = true; break; }
             if (on_x) { lx = lnew; Px += negx ? -fvox : fvox; }
@@ -165,11 +173,10 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
         if (cross) {
             // early termination where the ray enters another block, per batch and for
             // the ray: a batch whose every transmission is exactly zero would only add
-            // exact zeros (its own walk ends here, before this segment)
+            // exact zeros (its own walk ends here, after this segment)
 #pragma unroll
             for (int q = 0; q < NB; ++q)
                 if (((live >> q) & 1u) && all_opaque<8>(T + 8 * q)) live &= ~(1u << q);
-            ends &= live;
             if (live == 0u) break;
             const int bxn = bxc + (on_x ? sx : 0), bzn = bzc + (on_x ? 0 : sz);
             if ((unsigned)bxn >= (unsigned)G.nbx || (unsigned)bzn >= (unsigned)G.nbz) {
@@ -226,14 +233,6 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
                             (size_t)(level_offset(m) + (lz >> sh) * (DEX_BLOCK >> m) + (lx >> sh)) * REC;
                 }
                 next_fresh = live;
-            }
-        }
-        // integrate the voxels that ended on this plane (records loaded at the top)
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            if ((ends >> q) & 1u) {
-                segments<8>(rec[q].S, rec[q].chi, nl2[q], I + 8 * q, T + 8 * q);
-                if (COUNT) nseg += (pos >> q) & 1u;
             }
         }
         if (last) break;
@@ -301,7 +300,9 @@ __global__ void __launch_bounds__(256, 2) k_solve_hdda_mb(const HddaParams P)
     G.chain = P.chain;
     G.cap_active = P.cap_active;
     G.batch_base = P.bricks;
-    set_bands(G, P.n_band, P.band);
+    set_box_full(G);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) G.band[q] = P.band[q];
     long long slot_off[NB];
 #pragma unroll
     for (int q = 0; q < NB; ++q) slot_off[q] = (long long)max(bq[q], 0) * P.cap_active * P.chain * REC;

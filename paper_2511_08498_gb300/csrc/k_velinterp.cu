@@ -28,6 +28,7 @@ struct VelModel {
     static constexpr bool kPerBatch = true;
     static constexpr int kMinBlocks = 4;
     static constexpr bool kEarlyLoad = false;
+    static constexpr bool kZeroNoop = false;  // profile parameters of zero are not a no-op
     struct Params {
         int unused;
     };
