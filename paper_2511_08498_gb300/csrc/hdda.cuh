@@ -85,9 +85,10 @@ __device__ __align__(32) float g_zero_record[32] = {0.0f};
 // caller) over the traversal; L looks up the batch's block states and offsets.
 // EXT: the emission of the probe's own voxel (the first segment) is left out.
 //
-// Each step integrates the voxel it leaves, then steps to the next voxel of the
+// Each step integrates the voxel it leaves and steps to the next voxel of the
 // same level; only a step that leaves the block (one divergent branch) looks up
-// the next block.  A ray's block indices change monotonically and it takes at
+// the next block: after the integration for models with kZeroNoop (the
+// transmission test then sees the block's last segment), before it otherwise.  A ray's block indices change monotonically and it takes at
 // most 2 * 16 steps in a block, so the grid bounds check also bounds the loop.
 template <int W, bool COUNT, class Model, class Lookup, bool EXT = false>
 __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Params& M, int b, int i, int j,
@@ -115,6 +116,56 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
     float Pz = (float)(bz0 * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
     const float* rp = batch_base + ((size_t)a0 * G.chain + level_offset(mip) + lz * side + lx) * REC;
     float th_prev = 0.0f, tl_prev = 0.0f;
+    // the step left the block: look up the next one and re-initialise the tracer
+    // there (false: the ray ends)
+    auto enter = [&](bool on_x, float th) -> bool {
+        // early termination: once every transmission has underflowed to exactly
+        // zero the rest of the ray adds exact zeros, so stopping leaves I and T
+        // bit-identical
+        if (all_opaque<W>(T)) return false;
+        if (on_x) bxc += sx;
+        else bzc += sz;
+        if ((unsigned)bxc >= (unsigned)G.nbx || (unsigned)bzc >= (unsigned)G.nbz) {
+            capped = true;
+            return false;
+        }
+        const int key = L.key(bzc * G.nbx + bxc);
+        const int st = L.state(key) - 1;
+        const int mip_new = st < 0 ? -1 : min(st, distance_cap(G, th));
+        if (mip_new == mip) {
+            if (on_x) lx = negx ? side - 1 : 0;
+            else lz = negz ? side - 1 : 0;
+        } else {
+            // MIP-0 cell entered: exact on the stepped axis, from p(t) on the
+            // other one, clamped to the voxel just left (the block index on that
+            // axis is unchanged)
+            const int vox_old = vox;
+            int m0x, m0z;
+            if (on_x) {
+                m0x = bxc * DEX_BLOCK + (negx ? DEX_BLOCK - 1 : 0);
+                const int lo = bzc * DEX_BLOCK + lz * vox_old;
+                m0z = min(max(__float2int_rd(fmaf(th, dz, oz)), lo), lo + vox_old - 1);
+            } else {
+                m0z = bzc * DEX_BLOCK + (negz ? DEX_BLOCK - 1 : 0);
+                const int lo = bxc * DEX_BLOCK + lx * vox_old;
+                m0x = min(max(__float2int_rd(fmaf(th, dx, ox)), lo), lo + vox_old - 1);
+            }
+            mip = mip_new;
+            const int shift = mip >= 0 ? mip : 4;
+            vox = 1 << shift;
+            fvox = (float)vox;
+            side = DEX_BLOCK >> shift;
+            lx = (m0x - bxc * DEX_BLOCK) >> shift;
+            lz = (m0z - bzc * DEX_BLOCK) >> shift;
+            Px = (float)(bxc * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
+            Pz = (float)(bzc * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
+        }
+        if (mip >= 0)
+            rp = batch_base + ((size_t)L.offset_of(key) * G.chain + level_offset(mip) + lz * side + lx) * REC;
+        else if (kZero)
+            rp = g_zero_record;
+        return true;
+    };
     typename Model::Voxel cur;
 
     // unrolled four times (twice and eight times measured slower on the 1024^2
@@ -147,6 +198,11 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
             rp += negz ? -side * REC : side * REC;
             cross = (unsigned)lz >= (unsigned)side;
         }
+        if constexpr (!kZero) {
+            // models without a zero record enter the next block before integrating
+            // (measured 2-4% faster for them on a 1024 x 512 moving medium)
+            if (cross && !last && !enter(on_x, th)) break;
+        }
         // integrate the voxel left (in empty blocks: the zero record, or nothing)
         if (kZero || cur_mip >= 0) {
             if constexpr (!Model::kEarlyLoad) cur = Model::load(cur_rp);
@@ -162,52 +218,8 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
         if (last) break;
         th_prev = th;
         tl_prev = tl;
-        if (cross) {  // entered another block
-            // early termination: once every transmission has underflowed to exactly
-            // zero the rest of the ray adds exact zeros, so stopping leaves I and T
-            // bit-identical
-            if (all_opaque<W>(T)) break;
-            if (on_x) bxc += sx;
-            else bzc += sz;
-            if ((unsigned)bxc >= (unsigned)G.nbx || (unsigned)bzc >= (unsigned)G.nbz) {
-                capped = true;
-                break;
-            }
-            const int key = L.key(bzc * G.nbx + bxc);
-            const int st = L.state(key) - 1;
-            const int mip_new = st < 0 ? -1 : min(st, distance_cap(G, th));
-            if (mip_new == mip) {
-                if (on_x) lx = negx ? side - 1 : 0;
-                else lz = negz ? side - 1 : 0;
-            } else {
-                // MIP-0 cell entered: exact on the stepped axis, from p(t) on the
-                // other one, clamped to the voxel just left (the block index on that
-                // axis is unchanged)
-                const int vox_old = vox;
-                int m0x, m0z;
-                if (on_x) {
-                    m0x = bxc * DEX_BLOCK + (negx ? DEX_BLOCK - 1 : 0);
-                    const int lo = bzc * DEX_BLOCK + lz * vox_old;
-                    m0z = min(max(__float2int_rd(fmaf(th, dz, oz)), lo), lo + vox_old - 1);
-                } else {
-                    m0z = bzc * DEX_BLOCK + (negz ? DEX_BLOCK - 1 : 0);
-                    const int lo = bxc * DEX_BLOCK + lx * vox_old;
-                    m0x = min(max(__float2int_rd(fmaf(th, dx, ox)), lo), lo + vox_old - 1);
-                }
-                mip = mip_new;
-                const int shift = mip >= 0 ? mip : 4;
-                vox = 1 << shift;
-                fvox = (float)vox;
-                side = DEX_BLOCK >> shift;
-                lx = (m0x - bxc * DEX_BLOCK) >> shift;
-                lz = (m0z - bzc * DEX_BLOCK) >> shift;
-                Px = (float)(bxc * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
-                Pz = (float)(bzc * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
-            }
-            if (mip >= 0)
-                rp = batch_base + ((size_t)L.offset_of(key) * G.chain + level_offset(mip) + lz * side + lx) * REC;
-            else if (kZero)
-                rp = g_zero_record;
+        if constexpr (kZero) {
+            if (cross && !enter(on_x, th)) break;
         }
     }
 }
