@@ -18,8 +18,11 @@
 //    others, clamped to the voxel just left, then floored to the new voxel size;
 //  * a block first entered at ray parameter t uses level
 //    min(block level, #{band[m-1] <= t}) (the distance limit).
-// Plane parameters are two-float sums (AxisParam), t never decreases, lengths
-// are clamped at zero, and every ray has a step cap (DEX_ERR_TRAVERSAL_CAP).
+// Plane parameters are two-float sums (AxisParam), t never decreases and
+// lengths are clamped at zero; a ray that would step out of the grid before its
+// exit plane sets DEX_ERR_TRAVERSAL_CAP.  (Clipping rays to the box around the
+// non-empty blocks, as the 2D solver does, bought nothing on the 256^3 workload
+// once the box had to be found in every CTA.)
 #include "dex_internal.h"
 
 namespace dex {
@@ -43,25 +46,32 @@ __device__ __forceinline__ int block_state3(const unsigned long long* words, int
     return (int)((words[wi] >> sh) & 7ull);
 }
 
+// A record of zeros (any record format up to 32 floats): integrating it changes
+// nothing (tau = 0: 2^x = 1, 1 - e^{-tau} = 0), so rays read it in empty blocks
+// instead of branching around the update.
+__device__ __align__(32) float g_zero_record3[32] = {0.0f};
+
 // Highest level a block first entered at ray parameter t may use: the number of
-// distance thresholds band[m-1] <= t, and never above the chains' top level
+// distance thresholds band[m-1] <= t (padded to four by the launcher), and never
+// above the chains' top level
 __device__ __forceinline__ int distance_cap3(const Hdda3Params& P, float t)
 {
-    if (P.n_band < 0) return P.max_mip;
-    int m = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) m += (q < P.n_band && P.band[q] <= t) ? 1 : 0;
+    const int m = (P.band[0] <= t) + (P.band[1] <= t) + (P.band[2] <= t) + (P.band[3] <= t);
     return min(m, P.max_mip);
 }
 
+// One ray from the centre of cell (i, j, k).  Each step integrates the voxel it
+// leaves and steps to the next voxel of the same level; only a step that leaves
+// the block (one divergent branch) looks up the next block, after the
+// integration.  Block indices change monotonically and a ray takes at most
+// 3 * 8 steps in a block, so the grid bounds check also bounds the loop.
 template <int W, bool COUNT, int ST>
-__device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __restrict__ base, int i, int j, int k,
-                                           int bx0, int by0, int bz0, int a0, int mip0, float dx, float dy, float dz,
-                                           const unsigned long long* words, float* I, float* T, unsigned int& nseg,
-                                           bool& capped)
+__device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __restrict__ base,
+                                           int i, int j, int k, int bx0, int by0, int bz0, int a0, int mip0, float dx,
+                                           float dy, float dz, const unsigned long long* words, float* I, float* T,
+                                           unsigned int& nseg, bool& capped)
 {
     constexpr int REC = RecFmt<W, ST>::kStride;
-    const int cap = 2 * (P.nx + P.ny + P.nz) + 64;
     const float ox = (float)i + 0.5f, oy = (float)j + 0.5f, oz = (float)k + 0.5f;
     const bool negx = dx < 0.0f, negy = dy < 0.0f, negz = dz < 0.0f;
     const int sx = negx ? -1 : 1, sy = negy ? -1 : 1, sz = negz ? -1 : 1;
@@ -85,9 +95,7 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
     for (int it = 0;; ++it) {
         // float32 records: issued at the top of the step (256-bit loads), so that the
         // stepping and crossing bookkeeping hides their latency
-        if constexpr (ST == kStoreF32) {
-            if (mip >= 0) r = RecFmt<W, ST>::load(rp);
-        }
+        if constexpr (ST == kStoreF32) r = RecFmt<W, ST>::load(rp);
         const float tnx = Px * ax.ih, tny = Py * ay.ih, tnz = Pz * az.ih;
         const int axis = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
         const float th = axis == 0 ? tnx : (axis == 1 ? tny : tnz);
@@ -96,80 +104,75 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
         const bool last = th >= t2;
         const int cur_mip = mip;
         const float* cur_rp = rp;
-        if (!last) {
-            if (it >= cap) { capped = true; break; }
-            // the step on the chosen axis, written as selects (no divergent branch
-            // when the lanes of a warp step on different axes)
-            const float fv = (float)vox;
-            const bool a0 = axis == 0, a1 = axis == 1;
-            lx += a0 ? sx : 0;
-            ly += a1 ? sy : 0;
-            lz += (!a0 && !a1) ? sz : 0;
-            Px = a0 ? (negx ? Px - fv : Px + fv) : Px;
-            Py = a1 ? (negy ? Py - fv : Py + fv) : Py;
-            Pz = (!a0 && !a1) ? (negz ? Pz - fv : Pz + fv) : Pz;
-            const int st_ax = a0 ? 1 : (a1 ? side : side * side);
-            const bool ng = a0 ? negx : (a1 ? negy : negz);
-            rp += (ng ? -st_ax : st_ax) * REC;
-            const int la = a0 ? lx : (a1 ? ly : lz);
-            const bool cross = (unsigned)la >= (unsigned)side;
-            // early termination where the ray enters another block, once every
-            // transmission is exactly zero (the rest adds exact zeros: bit-identical)
-            if (cross && all_opaque<W>(T)) break;
-            if (cross) {
-                const int bxn = bxc + (axis == 0 ? sx : 0), byn = byc + (axis == 1 ? sy : 0),
-                          bzn = bzc + (axis == 2 ? sz : 0);
-                if ((unsigned)bxn >= (unsigned)P.nbx || (unsigned)byn >= (unsigned)P.nby ||
-                    (unsigned)bzn >= (unsigned)P.nbz) {
-                    capped = true;
-                    break;
-                }
-                const int blk = (bzn * P.nby + byn) * P.nbx + bxn;
-                const int st = block_state3(words, blk) - 1;
-                const int mip_new = st < 0 ? -1 : min(st, distance_cap3(P, th));
-                if (mip_new == mip) {
-                    if (axis == 0) lx = negx ? side - 1 : 0;
-                    else if (axis == 1) ly = negy ? side - 1 : 0;
-                    else lz = negz ? side - 1 : 0;
-                } else {
-                    // MIP-0 cell entered: exact on the stepped axis, from p(t) on the two
-                    // others, clamped to the voxel just left
-                    const int vo = vox;
-                    const int lox = bxc * B3 + lx * vo, loy = byc * B3 + ly * vo, loz = bzc * B3 + lz * vo;
-                    const int m0x = axis == 0 ? bxn * B3 + (negx ? B3 - 1 : 0)
-                                              : min(max(__float2int_rd(fmaf(th, dx, ox)), lox), lox + vo - 1);
-                    const int m0y = axis == 1 ? byn * B3 + (negy ? B3 - 1 : 0)
-                                              : min(max(__float2int_rd(fmaf(th, dy, oy)), loy), loy + vo - 1);
-                    const int m0z = axis == 2 ? bzn * B3 + (negz ? B3 - 1 : 0)
-                                              : min(max(__float2int_rd(fmaf(th, dz, oz)), loz), loz + vo - 1);
-                    mip = mip_new;
-                    const int shift = mip >= 0 ? mip : 3;
-                    vox = 1 << shift;
-                    side = B3 >> shift;
-                    lx = (m0x - bxn * B3) >> shift;
-                    ly = (m0y - byn * B3) >> shift;
-                    lz = (m0z - bzn * B3) >> shift;
-                    Px = (float)(bxn * B3 + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
-                    Py = (float)(byn * B3 + (ly + (negy ? 0 : 1)) * vox - j) - 0.5f;
-                    Pz = (float)(bzn * B3 + (lz + (negz ? 0 : 1)) * vox - k) - 0.5f;
-                }
-                bxc = bxn;
-                byc = byn;
-                bzc = bzn;
-                if (mip >= 0) {
-                    const int a = P.block_offset[blk];
-                    rp = base + ((size_t)a * P.chain + level_offset3(mip) + (lz * side + ly) * side + lx) * REC;
-                }
-            }
-        }
-        if (cur_mip >= 0) {
-            if constexpr (ST != kStoreF32) r = RecFmt<W, ST>::template load<false>(cur_rp);
-            segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
-            if (COUNT) nseg += (th > th_prev);
-        }
+        // the step on the chosen axis, written as selects (no divergent branch
+        // when the lanes of a warp step on different axes); not used once last
+        const float fv = (float)vox;
+        const bool a0x = axis == 0, a1 = axis == 1;
+        lx += a0x ? sx : 0;
+        ly += a1 ? sy : 0;
+        lz += (!a0x && !a1) ? sz : 0;
+        Px = a0x ? (negx ? Px - fv : Px + fv) : Px;
+        Py = a1 ? (negy ? Py - fv : Py + fv) : Py;
+        Pz = (!a0x && !a1) ? (negz ? Pz - fv : Pz + fv) : Pz;
+        const int st_ax = a0x ? 1 : (a1 ? side : side * side);
+        const bool ng = a0x ? negx : (a1 ? negy : negz);
+        rp += (ng ? -st_ax : st_ax) * REC;
+        const int la = a0x ? lx : (a1 ? ly : lz);
+        const bool cross = (unsigned)la >= (unsigned)side;
+        // integrate the voxel left (the zero record in empty blocks)
+        if constexpr (ST != kStoreF32) r = RecFmt<W, ST>::template load<false>(cur_rp);
+        segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
+        if (COUNT) nseg += (cur_mip >= 0) & (th > th_prev);
         if (last) break;
         th_prev = th;
         tl_prev = tl;
+        if (cross) {  // entered another block
+            // early termination: once every transmission is exactly zero the rest of
+            // the ray adds exact zeros (bit-identical)
+            if (all_opaque<W>(T)) break;
+            const int bxn = bxc + (axis == 0 ? sx : 0), byn = byc + (axis == 1 ? sy : 0),
+                      bzn = bzc + (axis == 2 ? sz : 0);
+            if ((unsigned)bxn >= (unsigned)P.nbx || (unsigned)byn >= (unsigned)P.nby ||
+                (unsigned)bzn >= (unsigned)P.nbz) {
+                capped = true;
+                break;
+            }
+            const int blk = (bzn * P.nby + byn) * P.nbx + bxn;
+            const int st = block_state3(words, blk) - 1;
+            const int mip_new = st < 0 ? -1 : min(st, distance_cap3(P, th));
+            if (mip_new == mip) {
+                if (axis == 0) lx = negx ? side - 1 : 0;
+                else if (axis == 1) ly = negy ? side - 1 : 0;
+                else lz = negz ? side - 1 : 0;
+            } else {
+                // MIP-0 cell entered: exact on the stepped axis, from p(t) on the two
+                // others, clamped to the voxel just left
+                const int vo = vox;
+                const int lox = bxc * B3 + lx * vo, loy = byc * B3 + ly * vo, loz = bzc * B3 + lz * vo;
+                const int m0x = axis == 0 ? bxn * B3 + (negx ? B3 - 1 : 0)
+                                          : min(max(__float2int_rd(fmaf(th, dx, ox)), lox), lox + vo - 1);
+                const int m0y = axis == 1 ? byn * B3 + (negy ? B3 - 1 : 0)
+                                          : min(max(__float2int_rd(fmaf(th, dy, oy)), loy), loy + vo - 1);
+                const int m0z = axis == 2 ? bzn * B3 + (negz ? B3 - 1 : 0)
+                                          : min(max(__float2int_rd(fmaf(th, dz, oz)), loz), loz + vo - 1);
+                mip = mip_new;
+                const int shift = mip >= 0 ? mip : 3;
+                vox = 1 << shift;
+                side = B3 >> shift;
+                lx = (m0x - bxn * B3) >> shift;
+                ly = (m0y - byn * B3) >> shift;
+                lz = (m0z - bzn * B3) >> shift;
+                Px = (float)(bxn * B3 + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
+                Py = (float)(byn * B3 + (ly + (negy ? 0 : 1)) * vox - j) - 0.5f;
+                Pz = (float)(bzn * B3 + (lz + (negz ? 0 : 1)) * vox - k) - 0.5f;
+            }
+            bxc = bxn;
+            byc = byn;
+            bzc = bzn;
+            rp = mip >= 0 ? base + ((size_t)P.block_offset[blk] * P.chain + level_offset3(mip) +
+                                    (lz * side + ly) * side + lx) * REC
+                          : g_zero_record3;
+        }
     }
 }
 
@@ -246,8 +249,12 @@ cudaError_t launch3(K kernel, dim3 grid, size_t smem, cudaStream_t s, const Hdda
 
 }  // namespace
 
-cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P)
+cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P0)
 {
+    // distance thresholds padded to four: +inf beyond n_band, 0 for no limit
+    Hdda3Params P = P0;
+    for (int q = 0; q < 4; ++q)
+        P.band[q] = P0.n_band < 0 ? 0.0f : (q < P0.n_band ? P0.band[q] : __builtin_huge_valf());
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
     const size_t smem = P.n_words <= kMaxStagedWords ? sizeof(unsigned long long) * (size_t)P.n_words : 0;
     const dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
