@@ -15,6 +15,8 @@ import torch
 from ._native import DexError, lib
 
 DEX_MAX_DIRS = 256
+# traversal modes of the static accelerated solve (dex_ctx_set_traversal)
+TRAVERSAL_PER_BATCH, TRAVERSAL_SHARED, TRAVERSAL_PAIRED = 0, 1, 2
 
 
 def _ptr(t):
@@ -52,10 +54,15 @@ class Context:
         self.stream = stream
         self._rc(lib().dex_ctx_set_stream(self.handle, ctypes.c_void_p(stream.cuda_stream)))
 
-    def set_traversal(self, shared: bool):
-        """Static accelerated solve at W = 8: one walk per ray and wavelength
-        batch (``shared=False``, the default) or one walk for two batches."""
-        self._rc(lib().dex_ctx_set_traversal(self.handle, 1 if shared else 0))
+    def set_traversal(self, mode):
+        """Static accelerated solve at W = 8 (``dex_ctx_set_traversal``): one walk per
+        ray and wavelength batch (``TRAVERSAL_PER_BATCH`` or False, the default), one
+        walk for two batches at their own levels (``TRAVERSAL_SHARED`` or True), or one
+        walk for the pair of batches b, n_batch - 1 - b on the smaller of their levels,
+        one thread carrying 16 wavelengths (``TRAVERSAL_PAIRED``)."""
+        if isinstance(mode, bool):
+            mode = TRAVERSAL_SHARED if mode else TRAVERSAL_PER_BATCH
+        self._rc(lib().dex_ctx_set_traversal(self.handle, int(mode)))
 
     def set_own_cell(self, include: bool):
         """Include (default) or leave out each probe's own-cell emission in the

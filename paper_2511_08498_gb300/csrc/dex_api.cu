@@ -206,8 +206,9 @@ int dex_ctx_destroy(dex_ctx* ctx)
 int dex_ctx_set_traversal(dex_ctx* ctx, int mode)
 {
     if (!ctx) return DEX_ERR_ARG;
-    if (mode != DEX_TRAVERSAL_PER_BATCH && mode != DEX_TRAVERSAL_SHARED)
-        return fail(ctx, DEX_ERR_ARG, "traversal mode must be DEX_TRAVERSAL_PER_BATCH or DEX_TRAVERSAL_SHARED");
+    if (mode != DEX_TRAVERSAL_PER_BATCH && mode != DEX_TRAVERSAL_SHARED && mode != DEX_TRAVERSAL_PAIRED)
+        return fail(ctx, DEX_ERR_ARG,
+                    "traversal mode must be DEX_TRAVERSAL_PER_BATCH, DEX_TRAVERSAL_SHARED or DEX_TRAVERSAL_PAIRED");
     ctx->traversal = mode;
     return ok(ctx);
 }
@@ -497,6 +498,10 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     P.I = I;
     P.seg_count = seg_count;
     P.status = ctx->status;
+    if (kind == 0 && P.traversal == DEX_TRAVERSAL_PAIRED && !dex::solve_hdda_paired_applies(P))
+        return fail(ctx, DEX_ERR_UNSUPPORTED,
+                    "the paired walk needs W = 8, the own-cell emission included and at most %d blocks",
+                    dex::kInfoMaxBlocks);
     if (int r = bind(ctx)) return r;
     cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
     if (e == cudaSuccess && I)

@@ -55,7 +55,7 @@ struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
                      // (band padded to four by pad_bands)
-    int traversal;   // DEX_TRAVERSAL_PER_BATCH or DEX_TRAVERSAL_SHARED (static model, W = 8)
+    int traversal;   // DEX_TRAVERSAL_PER_BATCH, _SHARED or _PAIRED (static model, W = 8)
     int exclude_own; // leave out each probe's own-voxel emission (static model, W = 8, float32)
     float band[4];
     long long n_cells;
@@ -232,6 +232,8 @@ cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& p);
 // one traversal per ray for up to four wavelength batches (k_hdda_mb.cu)
 bool solve_hdda_shared_applies(const HddaParams& p);
 cudaError_t launch_solve_hdda_shared(cudaStream_t s, const HddaParams& p);
+bool solve_hdda_paired_applies(const HddaParams& p);
+cudaError_t launch_solve_hdda_paired(cudaStream_t s, const HddaParams& p);
 
 // --------------------------------------------------- radiance cascades --
 struct RcParams {

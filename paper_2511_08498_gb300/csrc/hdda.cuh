@@ -74,6 +74,21 @@ namespace {
 __device__ __align__(32) float g_zero_record[32] = {0.0f};
 }  // namespace
 
+// Record load of a voxel model: Model::load(M, p) where the model declares it
+// (its records need the launch parameters, e.g. a second batch's offset),
+// Model::load(p) otherwise.
+template <class Model>
+__device__ __forceinline__ auto model_load(const typename Model::Params& M, const float* p)
+    -> decltype(Model::load(M, p))
+{
+    return Model::load(M, p);
+}
+template <class Model>
+__device__ __forceinline__ auto model_load(const typename Model::Params&, const float* p) -> decltype(Model::load(p))
+{
+    return Model::load(p);
+}
+
 // Voxel models: Model::kStride floats per voxel record, Model::kPerBatch whether
 // records differ per wavelength batch, Model::kEarlyLoad whether the record is
 // loaded at the top of each step, Model::kZeroNoop whether a record of zeros
@@ -169,13 +184,13 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
     typename Model::Voxel cur;
 
     // unrolled four times (twice and eight times measured slower on the 1024^2
-    // benchmark solve)
+    // benchmark solve, for the single- and the two-batch model)
 #pragma unroll 4
     for (int it = 0;; ++it) {
         // models with kEarlyLoad issue the current voxel's record before the
         // stepping and crossing bookkeeping, which then hides its latency
         if constexpr (Model::kEarlyLoad) {
-            if (kZero || mip >= 0) cur = Model::load(rp);
+            if (kZero || mip >= 0) cur = model_load<Model>(M, rp);
         }
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
@@ -205,7 +220,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
         }
         // integrate the voxel left (in empty blocks: the zero record, or nothing)
         if (kZero || cur_mip >= 0) {
-            if constexpr (!Model::kEarlyLoad) cur = Model::load(cur_rp);
+            if constexpr (!Model::kEarlyLoad) cur = model_load<Model>(M, cur_rp);
             Model::integrate(M, cur, b, -dx, -dz, len * kNegLog2e, I, T);
             if constexpr (EXT) {
                 if (it == 0) {

@@ -68,6 +68,10 @@ cudaError_t launch_hdda_kernel(K kernel, dim3 grid, size_t smem, cudaStream_t s,
 cudaError_t launch_solve_hdda(cudaStream_t s, const HddaParams& P)
 {
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
+    if (P.traversal == DEX_TRAVERSAL_PAIRED) {
+        if (!solve_hdda_paired_applies(P)) return cudaErrorNotSupported;
+        return launch_solve_hdda_paired(s, P);
+    }
     if (solve_hdda_shared_applies(P)) return launch_solve_hdda_shared(s, P);
     if (P.exclude_own) {
         // own-voxel emission left out: W = 8, float32 records (the MALI path)

@@ -113,5 +113,5 @@ def test_shared_walk_equals_per_batch_walk(ctx, storage, L, seed, thr, band, shi
 
 def test_traversal_mode_is_checked(ctx):
     from paper_2511_08498_gb300 import _native, api
-    assert _native.lib().dex_ctx_set_traversal(ctx.handle, 2) == 1   # DEX_ERR_ARG
+    assert _native.lib().dex_ctx_set_traversal(ctx.handle, 3) == 1   # DEX_ERR_ARG
     ctx.set_traversal(False)
