@@ -48,14 +48,22 @@ CHI_DS_MIN = 0.25
 BAND = [6.0, 24.0, 96.0]
 WORKLOAD = (f"sparse static-line atmosphere {NX}x{NZ}, 16^2 blocks, 40% empty, {N_LAMBDA} wavelengths, "
             f"{N_DIR} directions, VLM mip 0-{MAX_MIP}, IoD threshold {THR:g}, level distance limits "
-            f"{BAND}, HDDA, FP32")
+            f"{BAND}, HDDA with one walk per mirrored pair of wavelength batches, FP32")
+# walk of the timed step: one per pair of wavelength batches b, n_batch - 1 - b on the
+# smaller of their levels (on this atmosphere the pairs' levels agree in every block,
+# so J equals that of one walk per batch bit for bit)
+TIMED_WALK = "paired"
+WALK_NAMES = {"paired": "one per pair of wavelength batches b, n-1-b (16 wavelengths per thread)",
+              "per_batch": "one per wavelength batch",
+              "shared": "one per pair b, n-1-b, each batch integrated at its own levels"}
 # accelerated variants reported beside the timed step: (name, IoD threshold, distance
-# limits, brick storage 0 float32 / 1 bfloat16 / 2 float16, one walk shared by two
-# wavelength batches (True) or one walk per batch (False))
-VARIANTS = [("strict_iod_1e-3", THR_STRICT, BAND, 0, False), ("paper_iod_1", 1.0, BAND, 0, False),
-            ("unlimited_vlm", 1e30, BAND, 0, False), ("no_distance_limit_iod_1e-2", THR, None, 0, False),
-            ("bf16_bricks", THR, BAND, 1, False), ("f16_bricks", THR, BAND, 2, False),
-            ("shared_walk_iod_1e-2", THR, BAND, 0, True), ("shared_walk_unlimited_vlm", 1e30, BAND, 0, True)]
+# limits, brick storage 0 float32 / 1 bfloat16 / 2 float16, walk)
+VARIANTS = [("strict_iod_1e-3", THR_STRICT, BAND, 0, "paired"), ("paper_iod_1", 1.0, BAND, 0, "paired"),
+            ("unlimited_vlm", 1e30, BAND, 0, "paired"), ("no_distance_limit_iod_1e-2", THR, None, 0, "paired"),
+            ("bf16_bricks", THR, BAND, 1, "paired"), ("f16_bricks", THR, BAND, 2, "paired"),
+            ("per_batch_walk_iod_1e-2", THR, BAND, 0, "per_batch"),
+            ("per_batch_walk_unlimited_vlm", 1e30, BAND, 0, "per_batch"),
+            ("shared_walk_iod_1e-2", THR, BAND, 0, "shared")]
 # the bar a variant must meet to be quoted as the fastest acceptable one: J error
 # p99.9 <= 0.5% against the plain solve (the population error is checked separately)
 ERR_BAR_PCT = 0.5
@@ -76,6 +84,8 @@ def parse():
     ap.add_argument("--nx", type=int, default=1024, help="grid side (smaller sides for profiling captures)")
     ap.add_argument("--phase", default="all", choices=["all", "accel", "plain"],
                     help="accel/plain: time only that path (profiling captures)")
+    ap.add_argument("--traversal", default=TIMED_WALK, choices=["per_batch", "shared", "paired"],
+                    help="walk of the accelerated path in --phase accel (profiling captures)")
     args = ap.parse_args()
     global NX, NZ, WORKLOAD
     if args.nx != NX:
@@ -183,9 +193,10 @@ class Workload:
         self.api.synth_static_line(self.ctx, d["chi_c"], d["s_c"], d["s_l"], d["ratio"], d["dld"], d["dlam"],
                                    eta=self.eta, chi=self.chi)
 
-    def step(self, thr=THR, band=BAND, ev=None, count=False, storage=0, shared=False):
+    def step(self, thr=THR, band=BAND, ev=None, count=False, storage=0, traversal=TIMED_WALK):
         api = self.api
-        self.ctx.set_traversal(shared)
+        self.ctx.set_traversal({"per_batch": api.TRAVERSAL_PER_BATCH, "shared": api.TRAVERSAL_SHARED,
+                                "paired": api.TRAVERSAL_PAIRED}[traversal])
         self.synth()
         self.grid = api.grid_build(self.ctx, NX, NZ, self.eta, self.chi, out=self.grid)
         self.mips = api.mips_build(self.ctx, self.grid, self.eta, self.chi, W, MAX_MIP, thr, thr, CHI_DS_MIN,
@@ -213,9 +224,9 @@ class Workload:
 
 # ncu summary of the HDDA kernel's DRAM traffic on this workload, and the sources
 # whose hash it records: the figure is reported only while they are unchanged
-TRAFFIC_PROFILE = os.path.join("profiles", "k_solve_hdda_static_w8_1024_dram.md")
+TRAFFIC_PROFILE = os.path.join("profiles", "k_solve_hdda_pair_static_1024_dram.md")
 HDDA_SOURCES = [os.path.join("paper_2511_08498_gb300", "csrc", f)
-                for f in ("hdda.cuh", "k_hdda.cu", "k_hdda_mb.cu", "dex_common.cuh")]
+                for f in ("hdda.cuh", "k_hdda.cu", "k_hdda_pair.cu", "dex_common.cuh")]
 # ... and, from the internal header, the kernel's parameter structs
 HDDA_STRUCTS = (os.path.join("paper_2511_08498_gb300", "csrc", "dex_internal.h"), ("HddaParams",))
 
@@ -287,7 +298,7 @@ def native(args):
 
     if args.phase != "all":  # profiling capture: only the requested path, no report
         if args.phase == "accel":
-            time_steps(lambda ev: wl.step(ev=ev), args.steps, args.warmup, torch, flush)
+            time_steps(lambda ev: wl.step(ev=ev, traversal=args.traversal), args.steps, args.warmup, torch, flush)
         else:
             wl.step()
             probes = wl.probes()
@@ -354,14 +365,14 @@ def native(args):
 
     # accelerated variants, same protocol
     variants = {}
-    for name, thr, band, storage, shared in VARIANTS:
-        seg_v = wl.step(thr=thr, band=band, count=True, storage=storage, shared=shared)
+    for name, thr, band, storage, walk in VARIANTS:
+        seg_v = wl.step(thr=thr, band=band, count=True, storage=storage, traversal=walk)
         J_v = wl.J[:, probes.long()].double()
-        vt, vk = time_steps(lambda ev: wl.step(thr=thr, band=band, ev=ev, storage=storage, shared=shared),
+        vt, vk = time_steps(lambda ev: wl.step(thr=thr, band=band, ev=ev, storage=storage, traversal=walk),
                             max(2, min(args.steps, 3)), 1, torch, flush)
         v_s = sum(vt) / 1e3 / len(vt)
         variants[name] = {"iod_threshold": thr, "distance_limits": band, "storage": ["f32", "bf16", "f16"][storage],
-                          "walk": "shared by wavelength batches b, n-1-b" if shared else "one per wavelength batch",
+                          "walk": WALK_NAMES[walk],
                           "ms_per_step": v_s * 1e3, "hdda_ms": sum(vk) / len(vk),
                           "value": dense_seg_lambda / v_s, "speedup_vs_plain": plain_s / v_s,
                           "executed_fraction": int(seg_v.item()) * W / dense_seg_lambda,
@@ -416,7 +427,8 @@ def native(args):
                    "l2": "flushed between steps (256 MiB write); inputs and bricks also exceed L2",
                    "timing": "CUDA events per step on the launch stream, flush outside the events",
                    "parallelism": "one independent atmosphere per rank (weak scaling, no collective)"},
-        "roofline": {"bound": "alu", "kernel": "k_solve_hdda_t<8> (one walk per wavelength batch)", "achieved": achieved, "peak": sfu_peak,
+        "roofline": {"bound": "alu", "kernel": "k_solve_hdda_pair<F32> (one walk per mirrored pair of wavelength batches)",
+                     "achieved": achieved, "peak": sfu_peak,
                      "unit": "G seg-lambda updates/s", "frac": achieved / sfu_peak,
                      "traffic": measured_traffic(), "traffic_unit": "DRAM bytes per launch (ncu, one capture)",
                      "peak_basis": "measured 2^x throughput of the special-function units "
@@ -458,7 +470,7 @@ def native(args):
         best = max(within, key=lambda c: c[1])
         out["fastest_within_bar"] = {"variant": best[0], "speedup_vs_plain": best[1], "j_err_pct_p99.9": best[2],
                                      "bar": f"J error p99.9 <= {ERR_BAR_PCT}% vs the plain solve"}
-    ctx.set_traversal(False)
+    ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
     out["cascades"] = cascade_check(ctx, wl, torch, flush)
     if not args.no_populations and args.phase == "all":
         out["populations"] = population_check(ctx, torch)
