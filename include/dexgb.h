@@ -97,7 +97,8 @@ int dex_ctx_set_stream(dex_ctx* ctx, void* stream);
  *     per-batch walk.  Needs W = 8, the own-cell emission included
  *     (dex_ctx_set_own_cell) and grids of at most 8192 blocks; otherwise
  *     dex_formal_solve_hdda returns DEX_ERR_UNSUPPORTED.  The executed segment
- *     count counts each segment of the walk once per batch of the pair.
+ *     count counts each segment of the walk once per batch of the pair.  The
+ *     3D solve (dex_formal_solve_hdda3) honours this mode too.
  * Any other mode -> DEX_ERR_ARG.  The setting belongs to the context.
  */
 /*
@@ -755,6 +756,10 @@ int dex_mips3_build(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, c
  *   J   device [n_lambda][nz][ny][nx] output; zeroed by the call, written at probe cells
  *   I   device [n_lambda][n_dir][nz][ny][nx] output or NULL (zeroed by the call)
  *   seg_count  device uint64 accumulator or NULL: adds the voxel segments integrated
+ * With the context's traversal set to DEX_TRAVERSAL_PAIRED (W = 8 and at most
+ * 8192 state words, else DEX_ERR_UNSUPPORTED) one walk serves each pair of
+ * batches b, n_batch - 1 - b on the smaller of their levels, as in the 2D
+ * solve; every other traversal setting gives one walk per batch.
  */
 int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, int W, int max_mip, int storage,
                            const float* bricks, const unsigned long long* state_words, const int* block_offset,

@@ -1340,6 +1340,7 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
     if (!std::isfinite(i_bc)) return fail(ctx, DEX_ERR_ARG, "i_bc not finite");
     dex::Hdda3Params P{};
     P.storage = storage;
+    P.traversal = ctx->traversal == DEX_TRAVERSAL_PAIRED ? DEX_TRAVERSAL_PAIRED : DEX_TRAVERSAL_PER_BATCH;
     P.n_band = -1;
     if (band != nullptr && n_band >= 0) {
         if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);
@@ -1379,6 +1380,8 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
     P.I = I;
     P.seg_count = seg_count;
     P.status = ctx->status;
+    if (P.traversal == DEX_TRAVERSAL_PAIRED && !dex::solve_hdda3_paired_applies(P))
+        return fail(ctx, DEX_ERR_UNSUPPORTED, "the paired 3D walk needs W = 8 and at most 8192 state words");
     if (int r = bind(ctx)) return r;
     cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
     if (e == cudaSuccess && I)

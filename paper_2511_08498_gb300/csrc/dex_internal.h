@@ -295,6 +295,7 @@ struct Mip3Params {
 
 struct Hdda3Params {
     int nx, ny, nz, nbx, nby, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active, storage;
+    int traversal;  // DEX_TRAVERSAL_PAIRED: one walk per pair of batches; otherwise one per batch
     int n_band;
     float band[4];
     long long n_cells;
@@ -317,6 +318,7 @@ cudaError_t launch_grid3_build(cudaStream_t s, int nx, int ny, int nz, int n_lam
                                int* block_offset, int* active, int* n_active);
 cudaError_t launch_mips3_build(cudaStream_t s, const Mip3Params& P);
 cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P);
+bool solve_hdda3_paired_applies(const Hdda3Params& P);
 
 cudaError_t launch_pack_planes(cudaStream_t s, long long n_cells, int n_lambda, int W,
                                const float* eta, const float* chi, float* planes, unsigned int* status);

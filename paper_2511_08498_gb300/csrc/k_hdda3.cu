@@ -65,8 +65,12 @@ __device__ __forceinline__ int distance_cap3(const Hdda3Params& P, float t)
 // the block (one divergent branch) looks up the next block, after the
 // integration.  Block indices change monotonically and a ray takes at most
 // 3 * 8 steps in a block, so the grid bounds check also bounds the loop.
-template <int W, bool COUNT, int ST>
-__device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __restrict__ base,
+//
+// NB = 2: the ray carries two wavelength batches whose bricks lie `off` floats
+// apart (I, T of 2 W wavelengths, the second batch's from index W); both are
+// integrated over every voxel of the walk.
+template <int W, bool COUNT, int ST, int NB = 1>
+__device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __restrict__ base, long long off,
                                            int i, int j, int k, int bx0, int by0, int bz0, int a0, int mip0, float dx,
                                            float dy, float dz, const unsigned long long* words, float* I, float* T,
                                            unsigned int& nseg, bool& capped)
@@ -89,13 +93,18 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
     float Py = (float)(by0 * B3 + (ly + (negy ? 0 : 1)) * vox - j) - 0.5f;
     float Pz = (float)(bz0 * B3 + (lz + (negz ? 0 : 1)) * vox - k) - 0.5f;
     const float* rp = base + ((size_t)a0 * P.chain + level_offset3(mip) + (lz * side + ly) * side + lx) * REC;
+    // the second batch's record (the zero record in empty blocks)
+    const float* rp2 = NB == 2 ? rp + off : nullptr;
     float th_prev = 0.0f, tl_prev = 0.0f;
 
-    Record<W> r;
+    Record<W> r, r2;
     for (int it = 0;; ++it) {
         // float32 records: issued at the top of the step (256-bit loads), so that the
         // stepping and crossing bookkeeping hides their latency
-        if constexpr (ST == kStoreF32) r = RecFmt<W, ST>::load(rp);
+        if constexpr (ST == kStoreF32) {
+            r = RecFmt<W, ST>::load(rp);
+            if constexpr (NB == 2) r2 = RecFmt<W, ST>::load(rp2);
+        }
         const float tnx = Px * ax.ih, tny = Py * ay.ih, tnz = Pz * az.ih;
         const int axis = (tnx <= tny && tnx <= tnz) ? 0 : (tny <= tnz ? 1 : 2);
         const float th = axis == 0 ? tnx : (axis == 1 ? tny : tnz);
@@ -104,6 +113,7 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
         const bool last = th >= t2;
         const int cur_mip = mip;
         const float* cur_rp = rp;
+        const float* cur_rp2 = rp2;
         // the step on the chosen axis, written as selects (no divergent branch
         // when the lanes of a warp step on different axes); not used once last
         const float fv = (float)vox;
@@ -117,11 +127,17 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
         const int st_ax = a0x ? 1 : (a1 ? side : side * side);
         const bool ng = a0x ? negx : (a1 ? negy : negz);
         rp += (ng ? -st_ax : st_ax) * REC;
+        if constexpr (NB == 2) rp2 += (ng ? -st_ax : st_ax) * REC;
         const int la = a0x ? lx : (a1 ? ly : lz);
         const bool cross = (unsigned)la >= (unsigned)side;
         // integrate the voxel left (the zero record in empty blocks)
+        const float nl2 = len * kNegLog2e;
         if constexpr (ST != kStoreF32) r = RecFmt<W, ST>::template load<false>(cur_rp);
-        segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
+        segments<W>(r.S, r.chi, nl2, I, T);
+        if constexpr (NB == 2) {
+            if constexpr (ST != kStoreF32) r2 = RecFmt<W, ST>::template load<false>(cur_rp2);
+            segments<W>(r2.S, r2.chi, nl2, I + W, T + W);
+        }
         if (COUNT) nseg += (cur_mip >= 0) & (th > th_prev);
         if (last) break;
         th_prev = th;
@@ -129,7 +145,7 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
         if (cross) {  // entered another block
             // early termination: once every transmission is exactly zero the rest of
             // the ray adds exact zeros (bit-identical)
-            if (all_opaque<W>(T)) break;
+            if (all_opaque<NB * W>(T)) break;
             const int bxn = bxc + (axis == 0 ? sx : 0), byn = byc + (axis == 1 ? sy : 0),
                       bzn = bzc + (axis == 2 ? sz : 0);
             if ((unsigned)bxn >= (unsigned)P.nbx || (unsigned)byn >= (unsigned)P.nby ||
@@ -172,22 +188,46 @@ __device__ __forceinline__ void trace_ray3(const Hdda3Params& P, const float* __
             rp = mip >= 0 ? base + ((size_t)P.block_offset[blk] * P.chain + level_offset3(mip) +
                                     (lz * side + ly) * side + lx) * REC
                           : g_zero_record3;
+            if constexpr (NB == 2) rp2 = mip >= 0 ? rp + off : g_zero_record3;
         }
     }
 }
 
-template <int W, bool COUNT, int ST>
-__global__ void __launch_bounds__(kThreads3, kMinBlocks3) k_solve_hdda3(const Hdda3Params P)
+// Packed 3-bit states of two batches, state by state the smaller (0 = empty
+// wins): the level map of a walk shared by the two.
+__device__ __forceinline__ unsigned long long min_states(unsigned long long a, unsigned long long b)
+{
+    unsigned long long m = 0ull;
+#pragma unroll
+    for (int q = 0; q < DEX_STATES_PER_WORD; ++q) {
+        const int sh = DEX_STATE_BITS * q;
+        const unsigned long long sa = (a >> sh) & 7ull, sb = (b >> sh) & 7ull;
+        m |= (sa < sb ? sa : sb) << sh;
+    }
+    return m;
+}
+
+// NB = 1: one CTA per (active block, wavelength batch).  NB = 2: one CTA per
+// (active block, pair of batches b, n_batch - 1 - b), walking once for both on
+// the smaller of their levels (the state words must fit in shared memory).
+template <int W, bool COUNT, int ST, int NB>
+__global__ void __launch_bounds__(kThreads3, NB == 1 ? kMinBlocks3 : 2) k_solve_hdda3(const Hdda3Params P)
 {
     extern __shared__ unsigned long long s_words[];
+    __shared__ float s_J3[NB == 2 ? 2 * W : 1][kThreads3];
     const int a0 = blockIdx.x;
     if (a0 >= *P.n_active) return;
-    const int b = blockIdx.y;
+    const int b = blockIdx.y, b2 = NB == 2 ? P.n_batch - 1 - blockIdx.y : b;
     const int tid = threadIdx.x;
     const unsigned long long* gw = P.words + (size_t)b * P.n_words;
-    const bool staged = P.n_words <= kMaxStagedWords;
+    const bool staged = NB == 2 || P.n_words <= kMaxStagedWords;
     if (staged) {
-        for (int q = tid; q < P.n_words; q += kThreads3) s_words[q] = gw[q];
+        if constexpr (NB == 2) {
+            const unsigned long long* gw2 = P.words + (size_t)b2 * P.n_words;
+            for (int q = tid; q < P.n_words; q += kThreads3) s_words[q] = min_states(gw[q], gw2[q]);
+        } else {
+            for (int q = tid; q < P.n_words; q += kThreads3) s_words[q] = gw[q];
+        }
         __syncthreads();
     }
     const unsigned long long* words = staged ? s_words : gw;
@@ -199,7 +239,9 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3) k_solve_hdda3(const Hd
         return;
     }
     constexpr int REC = RecFmt<W, ST>::kStride;
-    const float* base = P.bricks + (size_t)b * P.cap_active * P.chain * REC;
+    const size_t batch_floats = (size_t)P.cap_active * P.chain * REC;
+    const float* base = P.bricks + (size_t)b * batch_floats;
+    const long long off = (long long)(b2 - b) * (long long)batch_floats;
     const int mip0 = min(state0, distance_cap3(P, 0.0f));
     unsigned int nseg = 0;
     bool capped = false;
@@ -208,32 +250,36 @@ __global__ void __launch_bounds__(kThreads3, kMinBlocks3) k_solve_hdda3(const Hd
     for (int pc = tid; pc < kCells3; pc += kThreads3) {
         const int i = bx0 * B3 + (pc & 7), j = by0 * B3 + ((pc >> 3) & 7), k = bz0 * B3 + (pc >> 6);
         const size_t cell = ((size_t)k * P.ny + j) * P.nx + i;
-        float Jw[W];
+        // J of the probe: registers for one batch, shared memory for a pair (whose
+        // I and T take the registers)
+        float Jr[NB == 1 ? W : 1];
+        auto Jw = [&](int w) -> float& { return NB == 1 ? Jr[NB == 1 ? w : 0] : s_J3[w][tid]; };
 #pragma unroll
-        for (int w = 0; w < W; ++w) Jw[w] = 0.0f;
+        for (int w = 0; w < NB * W; ++w) Jw(w) = 0.0f;
         for (int q = 0; q < P.quad.n_dir; ++q) {
-            float I[W], T[W];
+            float I[NB * W], T[NB * W];
 #pragma unroll
-            for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
-            trace_ray3<W, COUNT, ST>(P, base, i, j, k, bx0, by0, bz0, a0, mip0, P.quad.dx[q], P.quad.dy[q],
-                                     P.quad.dz[q], words, I, T, nseg, capped);
+            for (int w = 0; w < NB * W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
+            trace_ray3<W, COUNT, ST, NB>(P, base, off, i, j, k, bx0, by0, bz0, a0, mip0, P.quad.dx[q], P.quad.dy[q],
+                                         P.quad.dz[q], words, I, T, nseg, capped);
             const float wk = P.quad.w[q];
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
+            for (int w = 0; w < NB * W; ++w) {
                 const float Iw = fmaf(T[w], P.i_bc, I[w]);
-                Jw[w] = fmaf(wk, Iw, Jw[w]);
-                const int l = b * W + w;
+                Jw(w) = fmaf(wk, Iw, Jw(w));
+                const int l = w < W ? b * W + w : b2 * W + (w - W);
                 if (P.I != nullptr && l < P.n_lambda) P.I[((size_t)l * P.quad.n_dir + q) * P.n_cells + cell] = Iw;
             }
         }
 #pragma unroll
-        for (int w = 0; w < W; ++w) {
-            const int l = b * W + w;
-            if (l < P.n_lambda) P.J[(size_t)l * P.n_cells + cell] = Jw[w];
+        for (int w = 0; w < NB * W; ++w) {
+            const int l = w < W ? b * W + w : b2 * W + (w - W);
+            if (l < P.n_lambda) P.J[(size_t)l * P.n_cells + cell] = Jw(w);
         }
     }
     if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
-    if (COUNT && P.seg_count != nullptr) atomicAdd(P.seg_count, (unsigned long long)nseg);
+    // the walk's segments, once per batch it carries
+    if (COUNT && P.seg_count != nullptr) atomicAdd(P.seg_count, (unsigned long long)NB * nseg);
 }
 
 template <typename K>
@@ -249,6 +295,11 @@ cudaError_t launch3(K kernel, dim3 grid, size_t smem, cudaStream_t s, const Hdda
 
 }  // namespace
 
+bool solve_hdda3_paired_applies(const Hdda3Params& P)
+{
+    return P.W == 8 && P.n_words <= kMaxStagedWords;
+}
+
 cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P0)
 {
     // distance thresholds padded to four: +inf beyond n_band, 0 for no limit
@@ -257,13 +308,45 @@ cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P0)
         P.band[q] = P0.n_band < 0 ? 0.0f : (q < P0.n_band ? P0.band[q] : __builtin_huge_valf());
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
     const size_t smem = P.n_words <= kMaxStagedWords ? sizeof(unsigned long long) * (size_t)P.n_words : 0;
-    const dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
     cudaError_t e = cudaSuccess;
+    if (P.traversal == DEX_TRAVERSAL_PAIRED) {
+        if (!solve_hdda3_paired_applies(P)) return cudaErrorNotSupported;
+        if (P.n_batch >= 2) {
+            const dim3 grid2((unsigned)P.cap_active, (unsigned)(P.n_batch / 2));
+            switch (P.storage) {
+#define DEX_LAUNCH3P(ST)                                                                     \
+    case ST:                                                                                 \
+        e = P.seg_count ? launch3(k_solve_hdda3<8, true, ST, 2>, grid2, smem, s, P)          \
+                        : launch3(k_solve_hdda3<8, false, ST, 2>, grid2, smem, s, P);        \
+        break;
+                DEX_LAUNCH3P(kStoreF32)
+                DEX_LAUNCH3P(kStoreBF16)
+                DEX_LAUNCH3P(kStoreF16)
+#undef DEX_LAUNCH3P
+                default: return cudaErrorInvalidValue;
+            }
+            if (e != cudaSuccess) return e;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (P.n_batch % 2 == 0) return cudaSuccess;
+        // the middle batch alone, by the per-batch walk on a view of that batch
+        const int m = P.n_batch / 2;
+        Hdda3Params Q = P0;
+        Q.traversal = DEX_TRAVERSAL_PER_BATCH;
+        Q.n_batch = 1;
+        Q.n_lambda = P.n_lambda - m * 8;
+        Q.bricks = P.bricks + (size_t)m * P.cap_active * P.chain * record_floats(8, P.storage);
+        Q.words = P.words + (size_t)m * P.n_words;
+        Q.J = P.J + (size_t)m * 8 * P.n_cells;
+        Q.I = P.I ? P.I + (size_t)m * 8 * P.quad.n_dir * P.n_cells : nullptr;
+        return launch_solve_hdda3(s, Q);
+    }
+    const dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
     switch (P.W * 4 + P.storage) {
 #define DEX_LAUNCH3(WW, ST)                                                                 \
     case WW * 4 + ST:                                                                       \
-        e = P.seg_count ? launch3(k_solve_hdda3<WW, true, ST>, grid, smem, s, P)            \
-                        : launch3(k_solve_hdda3<WW, false, ST>, grid, smem, s, P);          \
+        e = P.seg_count ? launch3(k_solve_hdda3<WW, true, ST, 1>, grid, smem, s, P)         \
+                        : launch3(k_solve_hdda3<WW, false, ST, 1>, grid, smem, s, P);       \
         break;
         DEX_LAUNCH3(1, kStoreF32)
         DEX_LAUNCH3(2, kStoreF32)

@@ -104,17 +104,22 @@ def report(n=256, n_lambda=16, n_az=16, n_incl=4, W=8, max_mip=3, iods=(1e-2, 1.
             nonlocal mp
             mp = api.mips3_build(ctx, grid, eta, chi, W, max_mip, iod, iod, 0.25, out=mp)
         t_build = _time(build, reps)
-        t_acc = _time(lambda: api.formal_solve_hdda3(ctx, grid, mp, dirs, w, J=J, band=BAND), reps)
-        _, _, sc = api.formal_solve_hdda3(ctx, grid, mp, dirs, w, J=J, band=BAND, count_segments=True)
-        ctx.check()
         lev = api.unpack_states(mp.words.cpu().numpy(), grid.n_blocks)
-        executed = int(sc.item()) * W
-        out[f"vlm_iod_{iod:g}"] = {
-            "ms": t_acc * 1e3, "mips_build_ms": t_build * 1e3, "seg_lambda_per_s": dense / t_acc,
-            "speedup_vs_plain": t_plain / t_acc, "executed_fraction": executed / dense,
-            "ex2_frac": executed / t_acc / peak,
-            "level_counts": {str(L): int((lev == L).sum()) for L in range(-1, max_mip + 1)},
-            "j_err_pct_vs_plain": _err(J[:, cells.long()], ref)}
+        # one walk per wavelength batch, and one per mirror pair of batches on the
+        # smaller of the pair's levels
+        for walk, mode in (("", api.TRAVERSAL_PER_BATCH), ("_paired", api.TRAVERSAL_PAIRED)):
+            ctx.set_traversal(mode)
+            t_acc = _time(lambda: api.formal_solve_hdda3(ctx, grid, mp, dirs, w, J=J, band=BAND), reps)
+            _, _, sc = api.formal_solve_hdda3(ctx, grid, mp, dirs, w, J=J, band=BAND, count_segments=True)
+            ctx.check()
+            ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+            executed = int(sc.item()) * W
+            out[f"vlm_iod_{iod:g}{walk}"] = {
+                "ms": t_acc * 1e3, "mips_build_ms": t_build * 1e3, "seg_lambda_per_s": dense / t_acc,
+                "speedup_vs_plain": t_plain / t_acc, "executed_fraction": executed / dense,
+                "ex2_frac": executed / t_acc / peak,
+                "level_counts": {str(L): int((lev == L).sum()) for L in range(-1, max_mip + 1)},
+                "j_err_pct_vs_plain": _err(J[:, cells.long()], ref)}
         del mp
     return out
 
