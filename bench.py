@@ -555,7 +555,14 @@ def population_check(ctx, torch):
     dev = {k: torch.from_numpy(np.ascontiguousarray(m[k]).reshape(-1)).cuda() for k in ("temperature", "ne", "nh")}
     live = torch.from_numpy(m["temperature"].reshape(-1) > 0).cuda()
 
-    def run(accelerated, iod):
+    # each line's samples fill whole batches (40 = 5 x 8): the paired walk pairs a
+    # line's mirrored batches with each other, the continuum's two batches together
+    n_per_line = int(np.sum(tag == 0))
+    group = n_per_line // W if n_per_line % W == 0 else 0
+
+    def run(accelerated, iod, walk="paired"):
+        ctx.set_traversal(api.TRAVERSAL_PAIRED if walk == "paired" else api.TRAVERSAL_PER_BATCH)
+        ctx.set_pair_group(group)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -564,13 +571,18 @@ def population_check(ctx, torch):
         e1.record()
         e1.synchronize()
         ctx.check()
+        ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+        ctx.set_pair_group(0)
         return p, e0.elapsed_time(e1) / 1e3 / POP_ITERS
 
     ref, t_plain = run(False, THR)
     out = {"workload": f"three-level atom {POP_N}x{POP_N}, {lam.size} wavelengths, {POP_DIRS} directions, "
-                       f"{POP_ITERS} Lambda steps from LTE", "plain_s_per_iteration": t_plain}
-    for name, iod in (("iod_1e-2", THR), ("unlimited_vlm", 1e30)):
-        p, t = run(True, iod)
+                       f"{POP_ITERS} Lambda steps from LTE", "plain_s_per_iteration": t_plain,
+           "walk": f"accelerated runs: one walk per mirror pair of wavelength batches within groups of {group} "
+                   "batches (each line's batches paired with each other); per_batch_walk: one walk per batch"}
+    for name, iod, walk in (("iod_1e-2", THR, "paired"), ("unlimited_vlm", 1e30, "paired"),
+                            ("iod_1e-2_per_batch_walk", THR, "per_batch")):
+        p, t = run(True, iod, walk)
         e = ((p - ref).abs() / ref.abs().clamp_min(1e-300))[:, live].reshape(-1).double().cpu().numpy() * 100.0
         out[name] = {"s_per_iteration": t, "speedup_vs_plain": t_plain / t,
                      "pop_err_pct_vs_plain": {q: float(np.percentile(e, v)) for q, v in

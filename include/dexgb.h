@@ -84,16 +84,17 @@ int dex_ctx_set_stream(dex_ctx* ctx, void* stream);
  *     word per block); otherwise the per-batch walk runs.  On a GB300 it is the
  *     slower of the two on the static-line workload (its larger per-thread
  *     state halves the resident warps).
- *   DEX_TRAVERSAL_PAIRED: one walk per ray for each pair of batches b and
- *     n_batch - 1 - b (a line's batches lie symmetrically about its centre, so
- *     a pair sees the same part of the profile and tends to take the same
- *     levels); one thread carries the pair's 16 wavelengths.  The walk uses, in
+ *   DEX_TRAVERSAL_PAIRED: one walk per ray for each pair of batches: b and
+ *     n_batch - 1 - b by default, else as dex_ctx_set_pair_group sets (a line's
+ *     batches lie symmetrically about its centre, so a pair sees the same part
+ *     of the profile and tends to take the same levels); one thread carries
+ *     the pair's 16 wavelengths.  The walk uses, in
  *     every block, the smaller of the two batches' levels (Section 2.2), capped
  *     by the distance limits as usual (Section 4.1): no batch is integrated more
  *     coarsely than at its own levels, and where the two agree the result is
  *     that of the per-batch walk.  J and I equal, bit for bit, those of the
  *     per-batch walk given state words that hold the pair's minimum for both
- *     batches.  With an odd number of batches the middle one is solved by the
+ *     batches.  The middle batch of a group of odd size is solved by the
  *     per-batch walk.  Needs W = 8, the own-cell emission included
  *     (dex_ctx_set_own_cell) and grids of at most 8192 blocks; otherwise
  *     dex_formal_solve_hdda returns DEX_ERR_UNSUPPORTED.  The executed segment
@@ -118,6 +119,19 @@ int dex_ctx_set_own_cell(dex_ctx* ctx, int include);
 #define DEX_TRAVERSAL_SHARED 1
 #define DEX_TRAVERSAL_PAIRED 2
 int dex_ctx_set_traversal(dex_ctx* ctx, int mode);
+
+/*
+ * Which batches the paired walk (DEX_TRAVERSAL_PAIRED) pairs (context setting,
+ * default 0).  The batches are taken in consecutive groups of `group` batches
+ * (group = 0, or group >= n_batch: one group of all batches) and paired
+ * mirror-wise inside each group: batch g0 + q with g0 + size - 1 - q, where g0
+ * is the group's first batch and size its number of batches (the last group
+ * may be short); the middle batch of a group of odd size is solved alone.  A
+ * wavelength grid that holds several lines one after the other, each line's
+ * samples filling whole batches, pairs each line's batches with each other
+ * when group is the batches per line.  group < 0 -> DEX_ERR_ARG.
+ */
+int dex_ctx_set_pair_group(dex_ctx* ctx, int group);
 
 /*
  * Synchronise the context's stream, read and clear the device status word.

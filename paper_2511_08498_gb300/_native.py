@@ -27,6 +27,7 @@ PROTOTYPES = {
     "dex_ctx_destroy": (c_int, [c_void_p]),
     "dex_ctx_set_stream": (c_int, [c_void_p, c_void_p]),
     "dex_ctx_set_traversal": (c_int, [c_void_p, c_int]),
+    "dex_ctx_set_pair_group": (c_int, [c_void_p, c_int]),
     "dex_ctx_set_own_cell": (c_int, [c_void_p, c_int]),
     "dex_ctx_check": (c_int, [c_void_p]),
     "dex_last_error": (c_char_p, [c_void_p]),

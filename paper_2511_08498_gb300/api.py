@@ -64,6 +64,11 @@ class Context:
             mode = TRAVERSAL_SHARED if mode else TRAVERSAL_PER_BATCH
         self._rc(lib().dex_ctx_set_traversal(self.handle, int(mode)))
 
+    def set_pair_group(self, group: int):
+        """Pairs of the paired walk: mirror-wise within consecutive groups of
+        ``group`` wavelength batches, 0 for one group of all (``dex_ctx_set_pair_group``)."""
+        self._rc(lib().dex_ctx_set_pair_group(self.handle, int(group)))
+
     def set_own_cell(self, include: bool):
         """Include (default) or leave out each probe's own-cell emission in the
         plain and accelerated solves (``dex_ctx_set_own_cell``)."""

@@ -14,6 +14,7 @@ struct dex_ctx {
     cudaStream_t stream;
     unsigned int* status;  // device word, OR of DEX_ERR_* bits raised by kernels
     int traversal = DEX_TRAVERSAL_PER_BATCH;  // static accelerated solve: one walk per wavelength batch
+    int pair_group = 0;                        // paired walk: batches paired within groups of this many
     int own_cell = 1;                          // solvers include each probe's own-cell emission
     char msg[512];
 };
@@ -210,6 +211,14 @@ int dex_ctx_set_traversal(dex_ctx* ctx, int mode)
         return fail(ctx, DEX_ERR_ARG,
                     "traversal mode must be DEX_TRAVERSAL_PER_BATCH, DEX_TRAVERSAL_SHARED or DEX_TRAVERSAL_PAIRED");
     ctx->traversal = mode;
+    return ok(ctx);
+}
+
+int dex_ctx_set_pair_group(dex_ctx* ctx, int group)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (group < 0) return fail(ctx, DEX_ERR_ARG, "pair group must be >= 0, got %d", group);
+    ctx->pair_group = group;
     return ok(ctx);
 }
 
@@ -458,6 +467,7 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     P.storage = storage;
     P.n_band = -1;
     P.traversal = kind == 0 ? ctx->traversal : DEX_TRAVERSAL_PER_BATCH;
+    P.pair_group = ctx->pair_group;
     P.exclude_own = ctx->own_cell ? 0 : 1;
     if (P.exclude_own && (kind != 0 || W != 8 || storage != DEX_STORE_F32))
         return fail(ctx, DEX_ERR_UNSUPPORTED,
@@ -1341,6 +1351,7 @@ int dex_formal_solve_hdda3(dex_ctx* ctx, int nx, int ny, int nz, int n_lambda, i
     dex::Hdda3Params P{};
     P.storage = storage;
     P.traversal = ctx->traversal == DEX_TRAVERSAL_PAIRED ? DEX_TRAVERSAL_PAIRED : DEX_TRAVERSAL_PER_BATCH;
+    P.pair_group = ctx->pair_group;
     P.n_band = -1;
     if (band != nullptr && n_band >= 0) {
         if (n_band > 4) return fail(ctx, DEX_ERR_ARG, "at most 4 distance thresholds, got %d", n_band);

@@ -51,8 +51,39 @@ inline void pad_bands(int n_band, float* band)
         band[q] = n_band < 0 ? 0.0f : (q < n_band ? band[q] : __builtin_huge_valf());
 }
 
+// Pairs of wavelength batches walked together (DEX_TRAVERSAL_PAIRED): the
+// batches are paired mirror-wise within consecutive groups of `group` batches
+// (group <= 0 or >= n_batch: one group of all), b with g0 + size - 1 - (b - g0);
+// a group of odd size leaves its middle batch alone.
+__host__ __device__ inline int pair_group_size(int n_batch, int group)
+{
+    return group <= 0 || group > n_batch ? n_batch : group;
+}
+__host__ __device__ inline int pair_count(int n_batch, int group)
+{
+    const int g = pair_group_size(n_batch, group);
+    int n = 0;
+    for (int g0 = 0; g0 < n_batch; g0 += g) n += (n_batch - g0 < g ? n_batch - g0 : g) / 2;
+    return n;
+}
+__host__ __device__ inline void pair_batches(int p, int n_batch, int group, int& b1, int& b2)
+{
+    const int g = pair_group_size(n_batch, group);
+    for (int g0 = 0; g0 < n_batch; g0 += g) {
+        const int size = n_batch - g0 < g ? n_batch - g0 : g, np = size / 2;
+        if (p < np) {
+            b1 = g0 + p;
+            b2 = g0 + size - 1 - p;
+            return;
+        }
+        p -= np;
+    }
+    b1 = b2 = -1;
+}
+
 struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
+    int pair_group;  // DEX_TRAVERSAL_PAIRED: batches paired within groups of this many (0: one group)
     int n_band;      // < 0: no distance limit; else level m needs block entry t >= band[m-1]
                      // (band padded to four by pad_bands)
     int traversal;   // DEX_TRAVERSAL_PER_BATCH, _SHARED or _PAIRED (static model, W = 8)
@@ -296,6 +327,7 @@ struct Mip3Params {
 struct Hdda3Params {
     int nx, ny, nz, nbx, nby, nbz, n_lambda, W, n_batch, max_mip, chain, n_words, cap_active, storage;
     int traversal;  // DEX_TRAVERSAL_PAIRED: one walk per pair of batches; otherwise one per batch
+    int pair_group; // batches paired within groups of this many (0: one group), as HddaParams
     int n_band;
     float band[4];
     long long n_cells;

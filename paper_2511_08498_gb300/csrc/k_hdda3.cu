@@ -208,8 +208,8 @@ __device__ __forceinline__ unsigned long long min_states(unsigned long long a, u
 }
 
 // NB = 1: one CTA per (active block, wavelength batch).  NB = 2: one CTA per
-// (active block, pair of batches b, n_batch - 1 - b), walking once for both on
-// the smaller of their levels (the state words must fit in shared memory).
+// (active block, pair of batches, pair_batches), walking once for both on the
+// smaller of their levels (the state words must fit in shared memory).
 template <int W, bool COUNT, int ST, int NB>
 __global__ void __launch_bounds__(kThreads3, NB == 1 ? kMinBlocks3 : 2) k_solve_hdda3(const Hdda3Params P)
 {
@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(kThreads3, NB == 1 ? kMinBlocks3 : 2) k_solve_
     __shared__ float s_J3[NB == 2 ? 2 * W : 1][kThreads3];
     const int a0 = blockIdx.x;
     if (a0 >= *P.n_active) return;
-    const int b = blockIdx.y, b2 = NB == 2 ? P.n_batch - 1 - blockIdx.y : b;
+    int b = blockIdx.y, b2 = b;
+    if constexpr (NB == 2) pair_batches(blockIdx.y, P.n_batch, P.pair_group, b, b2);
     const int tid = threadIdx.x;
     const unsigned long long* gw = P.words + (size_t)b * P.n_words;
     const bool staged = NB == 2 || P.n_words <= kMaxStagedWords;
@@ -311,8 +312,9 @@ cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P0)
     cudaError_t e = cudaSuccess;
     if (P.traversal == DEX_TRAVERSAL_PAIRED) {
         if (!solve_hdda3_paired_applies(P)) return cudaErrorNotSupported;
-        if (P.n_batch >= 2) {
-            const dim3 grid2((unsigned)P.cap_active, (unsigned)(P.n_batch / 2));
+        const int n_pairs = pair_count(P.n_batch, P.pair_group);
+        if (n_pairs > 0) {
+            const dim3 grid2((unsigned)P.cap_active, (unsigned)n_pairs);
             switch (P.storage) {
 #define DEX_LAUNCH3P(ST)                                                                     \
     case ST:                                                                                 \
@@ -328,18 +330,24 @@ cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P0)
             if (e != cudaSuccess) return e;
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        if (P.n_batch % 2 == 0) return cudaSuccess;
-        // the middle batch alone, by the per-batch walk on a view of that batch
-        const int m = P.n_batch / 2;
-        Hdda3Params Q = P0;
-        Q.traversal = DEX_TRAVERSAL_PER_BATCH;
-        Q.n_batch = 1;
-        Q.n_lambda = P.n_lambda - m * 8;
-        Q.bricks = P.bricks + (size_t)m * P.cap_active * P.chain * record_floats(8, P.storage);
-        Q.words = P.words + (size_t)m * P.n_words;
-        Q.J = P.J + (size_t)m * 8 * P.n_cells;
-        Q.I = P.I ? P.I + (size_t)m * 8 * P.quad.n_dir * P.n_cells : nullptr;
-        return launch_solve_hdda3(s, Q);
+        // the middle batch of every group of odd size alone, by the per-batch walk
+        // on a view of that batch
+        const int g = pair_group_size(P.n_batch, P.pair_group);
+        for (int g0 = 0; g0 < P.n_batch; g0 += g) {
+            const int size = min(g, P.n_batch - g0);
+            if (size % 2 == 0) continue;
+            const int m = g0 + size / 2;
+            Hdda3Params Q = P0;
+            Q.traversal = DEX_TRAVERSAL_PER_BATCH;
+            Q.n_batch = 1;
+            Q.n_lambda = min(8, P.n_lambda - m * 8);
+            Q.bricks = P.bricks + (size_t)m * P.cap_active * P.chain * record_floats(8, P.storage);
+            Q.words = P.words + (size_t)m * P.n_words;
+            Q.J = P.J + (size_t)m * 8 * P.n_cells;
+            Q.I = P.I ? P.I + (size_t)m * 8 * P.quad.n_dir * P.n_cells : nullptr;
+            if ((e = launch_solve_hdda3(s, Q)) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     const dim3 grid((unsigned)P.cap_active, (unsigned)P.n_batch);
     switch (P.W * 4 + P.storage) {

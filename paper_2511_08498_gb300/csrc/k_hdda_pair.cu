@@ -5,18 +5,21 @@
 // The per-batch solver (k_hdda.cu) traces every ray once per batch of 8
 // wavelengths, and about two thirds of its instructions are the walk: plane
 // arithmetic, block crossings and level look-ups.  Here one thread carries the
-// 16 wavelengths of batches b and n_batch - 1 - b along one walk and integrates
-// both batches' records of every voxel it leaves.  A line's batches lie
-// symmetrically about its centre, so the two batches of a pair see the same
-// part of the profile and tend to take the same levels (on the benchmark's
-// static-line atmosphere every block's levels agree); the walk uses, in every
-// block, the smaller of the two levels (Section 2.2), capped by the distance
-// limits as usual.  No batch is integrated more coarsely than at its own levels.
+// 16 wavelengths of two batches along one walk and integrates both batches'
+// records of every voxel it leaves.  The batches pair mirror-wise within
+// consecutive groups (pair_batches: b with n_batch - 1 - b for one group of all
+// batches; a line's own batches when each group is one line's samples).  A
+// line's batches lie symmetrically about its centre, so the two batches of a
+// pair see the same part of the profile and tend to take the same levels (on
+// the benchmark's static-line atmosphere every block's levels agree); the walk
+// uses, in every block, the smaller of the two levels (Section 2.2), capped by
+// the distance limits as usual.  No batch is integrated more coarsely than at
+// its own levels.
 //
 // The walk and the update are those of k_solve_hdda_t (trace_ray) with a
 // two-record voxel model; J and I equal, bit for bit, those of the per-batch
-// walk given state words that hold the pair's minimum for both batches.  With
-// an odd number of batches the middle one is solved by the per-batch walk.
+// walk given state words that hold the pair's minimum for both batches.  The
+// middle batch of a group of odd size is solved by the per-batch walk.
 #include "hdda.cuh"
 
 namespace dex {
@@ -63,7 +66,7 @@ struct PairModel {
     }
 };
 
-// grid (cap_active, n_batch / 2 pairs), 256 threads; dynamic shared memory one
+// grid (cap_active, pair_count pairs), 256 threads; dynamic shared memory one
 // word per block: offset * 8 + the pair's minimum state
 template <int ST, bool COUNT>
 __global__ void __launch_bounds__(256, kPairMinBlocks) k_solve_hdda_pair(const HddaParams P)
@@ -74,7 +77,8 @@ __global__ void __launch_bounds__(256, kPairMinBlocks) k_solve_hdda_pair(const H
     __shared__ int s_box[4];
     const int a0 = blockIdx.x;
     if (a0 >= *P.n_active) return;
-    const int b1 = blockIdx.y, b2 = P.n_batch - 1 - blockIdx.y;
+    int b1, b2;
+    pair_batches(blockIdx.y, P.n_batch, P.pair_group, b1, b2);
     const int tid = threadIdx.x;
     const unsigned long long* w1 = P.words + (size_t)b1 * P.n_words;
     const unsigned long long* w2 = P.words + (size_t)b2 * P.n_words;
@@ -175,7 +179,7 @@ template <int ST>
 cudaError_t launch_pair(cudaStream_t s, const HddaParams& P)
 {
     const size_t smem = sizeof(int) * (size_t)P.nbx * P.nbz;
-    dim3 grid((unsigned)P.cap_active, (unsigned)(P.n_batch / 2));
+    dim3 grid((unsigned)P.cap_active, (unsigned)pair_count(P.n_batch, P.pair_group));
     auto kernel = P.seg_count ? k_solve_hdda_pair<ST, true> : k_solve_hdda_pair<ST, false>;
     if (smem > 24 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -196,7 +200,7 @@ bool solve_hdda_paired_applies(const HddaParams& P)
 cudaError_t launch_solve_hdda_paired(cudaStream_t s, const HddaParams& P)
 {
     if (P.cap_active == 0 || P.n_batch == 0) return cudaSuccess;
-    if (P.n_batch >= 2) {
+    if (pair_count(P.n_batch, P.pair_group) > 0) {
         cudaError_t e;
         switch (P.storage) {
             case kStoreF32: e = launch_pair<kStoreF32>(s, P); break;
@@ -206,18 +210,22 @@ cudaError_t launch_solve_hdda_paired(cudaStream_t s, const HddaParams& P)
         }
         if (e != cudaSuccess) return e;
     }
-    if (P.n_batch % 2 == 1) {
-        // the middle batch alone, by the per-batch walk on a view of that batch
-        const int m = P.n_batch / 2;
+    // the middle batch of every group of odd size alone, by the per-batch walk on
+    // a view of that batch
+    const int g = pair_group_size(P.n_batch, P.pair_group);
+    for (int g0 = 0; g0 < P.n_batch; g0 += g) {
+        const int size = min(g, P.n_batch - g0);
+        if (size % 2 == 0) continue;
+        const int m = g0 + size / 2;
         HddaParams Q = P;
         Q.traversal = DEX_TRAVERSAL_PER_BATCH;
         Q.n_batch = 1;
-        Q.n_lambda = P.n_lambda - m * 8;
+        Q.n_lambda = min(8, P.n_lambda - m * 8);
         Q.bricks = P.bricks + (size_t)m * P.cap_active * P.chain * record_floats(8, P.storage);
         Q.words = P.words + (size_t)m * P.n_words;
         Q.J = P.J + (size_t)m * 8 * P.n_cells;
         Q.I = P.I ? P.I + (size_t)m * 8 * P.quad.n_dir * P.n_cells : nullptr;
-        return launch_solve_hdda(s, Q);
+        if (cudaError_t e = launch_solve_hdda(s, Q)) return e;
     }
     return cudaSuccess;
 }

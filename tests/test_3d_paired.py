@@ -10,7 +10,8 @@ odd middle batch is solved alone.  So:
   off the middle of the wavelength grid so that the mirrored batches take
   different levels;
 * against the per-batch 3D walk given state words that hold the pair minimum
-  for both batches: bit for bit, for float32, bfloat16 and float16 bricks.
+  for both batches: bit for bit, for float32, bfloat16 and float16 bricks, and
+  with the batches paired within groups of two.
 """
 
 import numpy as np
@@ -38,8 +39,16 @@ def ctx():
     c.set_traversal(api.TRAVERSAL_PER_BATCH)
 
 
-def pair_min(lev):
-    return np.minimum(lev, lev[::-1])
+def pair_min(lev, group=0):
+    """Per batch, the smaller of its own levels and its partner's: mirror-wise
+    within consecutive groups of `group` batches (0: one group)."""
+    n = lev.shape[0]
+    g = n if group <= 0 or group > n else group
+    part = np.arange(n)
+    for g0 in range(0, n, g):
+        size = min(g, n - g0)
+        part[g0:g0 + size] = g0 + size - 1 - np.arange(size)
+    return np.minimum(lev, lev[part])
 
 
 def pack_states(lev, n_words):
@@ -67,14 +76,16 @@ def line3(ctx, nx, ny, nz, L, seed, shift):
     return eg, cg, e32, c32
 
 
-def solve(ctx, grid, mp, dirs, w, band, mode):
+def solve(ctx, grid, mp, dirs, w, band, mode, group=0):
     from paper_2511_08498_gb300 import api
     ctx.set_traversal(mode)
+    ctx.set_pair_group(group)
     try:
         J, I, seg = api.formal_solve_hdda3(ctx, grid, mp, dirs, w, band=band, want_intensity=True, i_bc=0.21)
         ctx.check()
     finally:
         ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+        ctx.set_pair_group(0)
     return J.cpu().numpy(), I.cpu().numpy()
 
 
@@ -102,8 +113,8 @@ def test_paired_3d_walk_matches_oracle(ctx, L, thr, band, shift):
     assert rel(J[:, probes], Jr).max() < 1e-5
 
 
-@pytest.mark.parametrize("storage", [0, 1, 2])
-def test_paired_3d_walk_equals_per_batch_walk_on_pair_minimum(ctx, storage):
+@pytest.mark.parametrize("storage,group", [(0, 0), (1, 0), (2, 0), (0, 2)])
+def test_paired_3d_walk_equals_per_batch_walk_on_pair_minimum(ctx, storage, group):
     from paper_2511_08498_gb300 import api
     nx, ny, nz, L = 40, 32, 48, 36                      # 4.5 batches: pairs (0, 4), (1, 3), batch 2 alone
     eg, cg, _, _ = line3(ctx, nx, ny, nz, L, synth.SEED_BASE + 198, 4.0)
@@ -111,9 +122,9 @@ def test_paired_3d_walk_equals_per_batch_walk_on_pair_minimum(ctx, storage):
     grid = api.grid3_build(ctx, nx, ny, nz, eg, cg)
     mp = api.mips3_build(ctx, grid, eg, cg, 8, 3, 0.1, 0.1, 0.25, storage=storage)
     band = [4.0, 12.0, 24.0]
-    Jc, Ic = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PAIRED)
+    Jc, Ic = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PAIRED, group=group)
     lev = api.unpack_states(mp.words.cpu().numpy(), grid.n_blocks)
-    mp.words.copy_(torch.from_numpy(pack_states(pair_min(lev), mp.words.shape[1])))
+    mp.words.copy_(torch.from_numpy(pack_states(pair_min(lev, group), mp.words.shape[1])))
     Jp, Ip = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PER_BATCH)
     assert np.array_equal(Ic, Ip)
     assert np.array_equal(Jc, Jp)

@@ -79,8 +79,10 @@ def test_without_distance_limits_the_averaging_shows(case):
     neighbourhood and the populations do move: evidence that the accelerated
     runs above really average (their agreement with the plain run is physics,
     not a disabled acceleration)."""
-    plain = run(case, False)
     acc = run(case, True, 0, 1e30, None)
     e = err_pct(case, acc)
     print("iod 1e30, no distance limits", e)
-    assert np.abs(acc - plain)[:, case["live"]].max() > 0
+    # measured on this instance: p50 10.6%, p99 689%, max 9456% -- coarse voxels
+    # next to the probes change the populations everywhere, by orders of
+    # magnitude more than the 1e-3% the distance-limited runs above allow
+    assert e["p50"] > 1.0 and e["p99"] > 100.0, e

@@ -44,10 +44,23 @@ def ctx():
     c.set_traversal(api.TRAVERSAL_PER_BATCH)
 
 
-def group_min(lev):
-    """Per batch b, the smaller of the levels of b and n_batch - 1 - b (-1, empty,
+def partners(n_batch, group=0):
+    """Partner of every batch under the paired walk's rule: mirror-wise within
+    consecutive groups of `group` batches (0: one group); a lone middle batch is
+    its own partner."""
+    g = n_batch if group <= 0 or group > n_batch else group
+    out = np.arange(n_batch)
+    for g0 in range(0, n_batch, g):
+        size = min(g, n_batch - g0)
+        for q in range(size):
+            out[g0 + q] = g0 + size - 1 - q
+    return out
+
+
+def group_min(lev, group=0):
+    """Per batch, the smaller of its own levels and its partner's (-1, empty,
     where either block is empty)."""
-    return np.minimum(lev, lev[::-1])
+    return np.minimum(lev, lev[partners(lev.shape[0], group)])
 
 
 def pack_states(lev, n_words):
@@ -77,15 +90,17 @@ def build(ctx, m, thr, storage, nx=NX, nz=NZ):
     return grid, mp
 
 
-def solve(ctx, grid, mp, dirs, w, band, mode, i_bc=0.0):
+def solve(ctx, grid, mp, dirs, w, band, mode, i_bc=0.0, group=0):
     from paper_2511_08498_gb300 import api
     ctx.set_traversal(mode)
+    ctx.set_pair_group(group)
     try:
         J, I, seg = api.formal_solve_hdda(ctx, grid, mp, dirs, w, want_intensity=True, count_segments=True,
                                           band=band, i_bc=i_bc)
         ctx.check()
     finally:
         ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+        ctx.set_pair_group(0)
     return J.cpu().numpy(), I.cpu().numpy(), int(seg.item())
 
 
@@ -182,3 +197,41 @@ def test_paired_walk_unsupported_configurations(ctx):
         ctx.set_own_cell(True)
         ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
     assert _native.lib().dex_ctx_set_traversal(ctx.handle, 3) == 1   # DEX_ERR_ARG
+
+
+def test_pair_rule():
+    assert list(partners(5)) == [4, 3, 2, 1, 0]
+    assert list(partners(5, 2)) == [1, 0, 3, 2, 4]
+    assert list(partners(12, 5)) == [4, 3, 2, 1, 0, 9, 8, 7, 6, 5, 11, 10]
+
+
+# (wavelengths, pair group): 5 batches in groups of 2 (pairs 0-1, 2-3, batch 4
+# alone) and of 3 (0-2, 3-4, batch 1 alone); 12 batches in groups of 5, the
+# layout of two 40-sample lines and a 16-sample continuum
+@pytest.mark.parametrize("L,group", [(40, 2), (40, 3), (96, 5)])
+def test_paired_walk_groups(ctx, L, group):
+    from paper_2511_08498_gb300 import api
+    m, er, cr = model(L, 497, 3.0)
+    dirs, w = synth.directions(8, offset=0.0)
+    band = [6.0, 24.0, 96.0]
+    grid, mp = build(ctx, m, 1e-2, 0)
+    Jc, Ic, _ = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PAIRED, i_bc=0.11, group=group)
+    lev = api.unpack_states(mp.words.cpu().numpy(), grid.n_blocks)
+    if L == 40:
+        # against the float64 oracle on the pair-minimum map of this grouping
+        levels, passes, st = omips.mip_chain(er, cr, 3, 1e-2, 1e-2, 0.25, mean="linear", stats=True)
+        empty = omips.block_empty(er, cr, 16)
+        lev_r = omips.block_levels(passes, empty, 16, W)
+        assert robust_level_mask(st, lev_r, W, 16, 3, 1e-2, 1e-2, 0.25).all()
+        assert np.array_equal(lev.reshape(lev_r.shape), lev_r)
+        lev_c = group_min(lev_r, group)
+        assert not np.array_equal(lev_c, lev_r)
+        probes = omips.probes_of_blocks(empty, 16)
+        Jr, Ir = lc.formal_solve_banded(levels, lev_c, 16, W, band, dirs, w, probes, i_bc=0.11, want_intensity=True)
+        assert rel(Ic[:, :, probes], Ir).max() < 1e-5
+        assert rel(Jc[:, probes], Jr).max() < 1e-5
+    # bit for bit against the per-batch walk on the same map
+    mp.words.copy_(torch.from_numpy(pack_states(group_min(lev, group), mp.words.shape[1])))
+    Jp, Ip, _ = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PER_BATCH, i_bc=0.11)
+    assert np.array_equal(Ic, Ip)
+    assert np.array_equal(Jc, Jp)
