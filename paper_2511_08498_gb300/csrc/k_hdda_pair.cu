@@ -68,7 +68,9 @@ struct PairModel {
 
 // grid (cap_active, pair_count pairs), 256 threads; dynamic shared memory one
 // word per block: offset * 8 + the pair's minimum state
-template <int ST, bool COUNT>
+// EXT: each probe's own-voxel emission is left out (the first segment of every
+// ray, as k_solve_hdda_t with EXT).
+template <int ST, bool COUNT, bool EXT>
 __global__ void __launch_bounds__(256, kPairMinBlocks) k_solve_hdda_pair(const HddaParams P)
 {
     using Model = PairModel<ST>;
@@ -153,8 +155,8 @@ __global__ void __launch_bounds__(256, kPairMinBlocks) k_solve_hdda_pair(const H
             I[w] = 0.0f;
             T[w] = 1.0f;
         }
-        trace_ray<16, COUNT, Model, InfoLookup>(G, M, b1, i, j, bx0, bz0, a0, mip0, dx, dz, InfoLookup{s_info}, I, T,
-                                                nseg, capped);
+        trace_ray<16, COUNT, Model, InfoLookup, EXT>(G, M, b1, i, j, bx0, bz0, a0, mip0, dx, dz, InfoLookup{s_info},
+                                                     I, T, nseg, capped);
         const float wk = P.quad.w[k];
 #pragma unroll
         for (int w = 0; w < 16; ++w) {
@@ -180,7 +182,8 @@ cudaError_t launch_pair(cudaStream_t s, const HddaParams& P)
 {
     const size_t smem = sizeof(int) * (size_t)P.nbx * P.nbz;
     dim3 grid((unsigned)P.cap_active, (unsigned)pair_count(P.n_batch, P.pair_group));
-    auto kernel = P.seg_count ? k_solve_hdda_pair<ST, true> : k_solve_hdda_pair<ST, false>;
+    auto kernel = P.exclude_own ? (P.seg_count ? k_solve_hdda_pair<ST, true, true> : k_solve_hdda_pair<ST, false, true>)
+                                : (P.seg_count ? k_solve_hdda_pair<ST, true, false> : k_solve_hdda_pair<ST, false, false>);
     if (smem > 24 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -194,7 +197,8 @@ cudaError_t launch_pair(cudaStream_t s, const HddaParams& P)
 bool solve_hdda_paired_applies(const HddaParams& P)
 {
     const long long n_blocks = (long long)P.nbx * P.nbz;
-    return P.traversal == DEX_TRAVERSAL_PAIRED && !P.exclude_own && P.W == 8 && n_blocks <= kInfoMaxBlocks;
+    return P.traversal == DEX_TRAVERSAL_PAIRED && P.W == 8 && n_blocks <= kInfoMaxBlocks &&
+           (!P.exclude_own || P.storage == kStoreF32);
 }
 
 cudaError_t launch_solve_hdda_paired(cudaStream_t s, const HddaParams& P)

@@ -188,15 +188,16 @@ def test_paired_walk_unsupported_configurations(ctx):
         with pytest.raises(api.DexError) as ex:
             api.formal_solve_hdda(ctx, grid, mp4, dirs, w)
         assert ex.value.code == 16   # DEX_ERR_UNSUPPORTED: W = 4
-        mp8 = api.mips_build(ctx, grid, eg, cg, 8, 3, 1e-2, 1e-2, 0.25)
+        mp8 = api.mips_build(ctx, grid, eg, cg, 8, 3, 1e-2, 1e-2, 0.25, storage=1)
         ctx.set_own_cell(False)
         with pytest.raises(api.DexError) as ex:
             api.formal_solve_hdda(ctx, grid, mp8, dirs, w)
-        assert ex.value.code == 16   # own-cell emission left out
+        assert ex.value.code == 16   # own-cell emission left out: float32 bricks only
     finally:
         ctx.set_own_cell(True)
         ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
     assert _native.lib().dex_ctx_set_traversal(ctx.handle, 3) == 1   # DEX_ERR_ARG
+    assert _native.lib().dex_ctx_set_pair_group(ctx.handle, -1) == 1  # DEX_ERR_ARG
 
 
 def test_pair_rule():
@@ -233,5 +234,26 @@ def test_paired_walk_groups(ctx, L, group):
     # bit for bit against the per-batch walk on the same map
     mp.words.copy_(torch.from_numpy(pack_states(group_min(lev, group), mp.words.shape[1])))
     Jp, Ip, _ = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PER_BATCH, i_bc=0.11)
+    assert np.array_equal(Ic, Ip)
+    assert np.array_equal(Jc, Jp)
+
+
+def test_paired_walk_without_own_cell(ctx):
+    """The own-cell emission left out (the MALI solves' Jext): the paired walk
+    equals the per-batch walk on the pair-minimum map bit for bit, pairs within
+    groups of two and a lone batch included."""
+    from paper_2511_08498_gb300 import api
+    m, _, _ = model(40, 498, 2.0)
+    dirs, w = synth.directions(8)
+    band = [6.0, 24.0, 96.0]
+    grid, mp = build(ctx, m, 1e-2, 0)
+    ctx.set_own_cell(False)
+    try:
+        Jc, Ic, _ = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PAIRED, group=2)
+        lev = api.unpack_states(mp.words.cpu().numpy(), grid.n_blocks)
+        mp.words.copy_(torch.from_numpy(pack_states(group_min(lev, 2), mp.words.shape[1])))
+        Jp, Ip, _ = solve(ctx, grid, mp, dirs, w, band, api.TRAVERSAL_PER_BATCH)
+    finally:
+        ctx.set_own_cell(True)
     assert np.array_equal(Ic, Ip)
     assert np.array_equal(Jc, Jp)
