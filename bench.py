@@ -523,13 +523,19 @@ def cascade_check(ctx, wl, torch, flush):
                      f"{RC_T0}, per-cascade level caps {RC_CAPS}, same input and grid as the timed step",
            "full_resolution_ms": t_full}
     ref = J0[:, mask].double()
+    # accelerated cascades with one walk per wavelength batch, and (suffix _paired)
+    # one walk per mirror pair of batches on the smaller of their levels
     for name, iod in (("iod_1e-2", THR), ("paper_iod_1", 1.0), ("unlimited_vlm", 1e30)):
         mp = api.mips_build(ctx, wl.grid, wl.eta, wl.chi, W, MAX_MIP, iod, iod, CHI_DS_MIN, log_mean=False)
-        t = timed(mp, RC_CAPS, J1)
-        rel = ((J1[:, mask].double() - ref).abs() / ref.abs().clamp_min(1e-30)).flatten().cpu().numpy() * 100.0
-        out[name] = {"ms": t, "speedup_vs_full_resolution": t_full / t,
-                     "j_err_pct_vs_full_resolution": {q: float(np.percentile(rel, p)) for q, p in
-                                                      (("p50", 50), ("p99", 99), ("p99.9", 99.9), ("max", 100))}}
+        for suffix, mode in (("", api.TRAVERSAL_PER_BATCH), ("_paired", api.TRAVERSAL_PAIRED)):
+            ctx.set_traversal(mode)
+            t = timed(mp, RC_CAPS, J1)
+            ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+            rel = ((J1[:, mask].double() - ref).abs() / ref.abs().clamp_min(1e-30)).flatten().cpu().numpy() * 100.0
+            out[name + suffix] = {"ms": t, "speedup_vs_full_resolution": t_full / t,
+                                  "j_err_pct_vs_full_resolution": {q: float(np.percentile(rel, p)) for q, p in
+                                                                   (("p50", 50), ("p99", 99), ("p99.9", 99.9),
+                                                                    ("max", 100))}}
     ctx.check()
     return out
 

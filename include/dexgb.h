@@ -592,6 +592,13 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
  * dex_formal_solve_hdda, so J is bit-identical for every configuration.
  * dex_batch_solve is dex_batch_solve_config with {ctas, 256, 1, 0, 0}.  Invalid
  * values -> DEX_ERR_ARG.
+ * With the context's traversal set to DEX_TRAVERSAL_PAIRED (W = 8; every grid
+ * of at most 8192 blocks, else DEX_ERR_UNSUPPORTED) the work units are each
+ * atmosphere's pairs of batches (dex_ctx_set_pair_group) and lone batches, and
+ * J equals that of dex_formal_solve_hdda's paired walk bit for bit; staging
+ * and occupancy then do not apply (one word per block is staged, at most 128
+ * registers a thread).  dex_batch_solve and dex_batch_solve_noalloc follow the
+ * setting too.
  */
 typedef struct {
     int ctas;
@@ -815,6 +822,10 @@ size_t dex_rc_workspace_floats(int nx, int nz, int n_lambda, int W, int n0);
  *   J             device [n_lambda][nz][nx] output: zeroed by the call, written at every
  *                 cell of every non-empty block
  *   seg_count     device uint64 accumulator or NULL: adds the voxel segments integrated
+ * With the context's traversal set to DEX_TRAVERSAL_PAIRED and W = 8, every
+ * interval walks once for each pair of batches (dex_ctx_set_pair_group) on the
+ * smaller of their levels, capped by the cascade's cap, lone batches alone;
+ * each segment then counts once per batch of the pair.
  */
 int dex_rc_solve(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip, int storage, const float* bricks,
                  const unsigned long long* state_words, const int* block_offset, int capacity, int n_cascades,

@@ -41,23 +41,40 @@ def _time(fn, reps=3):
     return best
 
 
+WALKS = {"per_batch": api.TRAVERSAL_PER_BATCH, "paired": api.TRAVERSAL_PAIRED}
+
+
+def run_config(ctx, items, W, cfg, queue=None, **kw):
+    """``dex_batch_solve_config`` with the knobs of ``cfg``; its ``walk`` (one walk
+    per batch, or one per mirror pair of batches) is set on the context for the
+    call."""
+    cfg = dict(cfg)
+    ctx.set_traversal(WALKS[cfg.pop("walk", "per_batch")])
+    try:
+        return api.batch_solve_config(ctx, items, W, queue=queue, **cfg, **kw)
+    finally:
+        ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+
+
 def tune_batch(ctx, items, W, reps=3, rounds=2):
     """Coordinate descent over the launch knobs of ``dex_batch_solve_config`` --
     persistent grid size, probes per work item (packet), work items per queue
-    claim (chunk), block-table staging and register budget -- starting from the
-    default configuration; every knob is swept with the others fixed, twice.
+    claim (chunk), block-table staging, register budget and the walk (one per
+    wavelength batch, or one per mirror pair of batches, W = 8) -- starting from
+    the default configuration; every knob is swept with the others fixed, twice.
     Returns ``{"best", "best_ms", "default", "default_ms", "trials"}``."""
     sms = torch.cuda.get_device_properties(ctx.device).multi_processor_count
     queue = torch.zeros(1, dtype=torch.int32, device=torch.device("cuda", ctx.device))
-    default = dict(ctas=3 * sms, packet=256, chunk=1, staging=0, occupancy=0)
-    space = [("ctas", [k * sms for k in (1, 2, 3, 4, 6, 8)]), ("packet", [256, 128, 64]), ("chunk", [1, 2, 4, 8, 16]),
+    default = dict(ctas=3 * sms, packet=256, chunk=1, staging=0, occupancy=0, walk="per_batch")
+    space = [("walk", ["per_batch", "paired"] if W == 8 else ["per_batch"]),
+             ("ctas", [k * sms for k in (1, 2, 3, 4, 6, 8)]), ("packet", [256, 128, 64]), ("chunk", [1, 2, 4, 8, 16]),
              ("staging", [0, 1]), ("occupancy", [0, 1] if W == 8 else [0])]
     trials = {}
 
     def timed(cfg):
         key = tuple(sorted(cfg.items()))
         if key not in trials:
-            trials[key] = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **cfg), reps)
+            trials[key] = _time(lambda: run_config(ctx, items, W, cfg, queue=queue), reps)
         return trials[key]
 
     best, best_t = dict(default), timed(default)
@@ -83,7 +100,7 @@ def tune_threshold(ctx, atms, W, cfg, thresholds=(0.0, 1e-4, 1e-3, 1e-2, 1.0, 1e
     for a in atms:
         a.build(max_mip=0)
     items = [a.item() for a in atms]
-    api.batch_solve_config(ctx, items, W, queue=queue, **cfg)
+    run_config(ctx, items, W, cfg, queue=queue)
     ctx.check()
     ref = [a.J.clone() for a in atms]
     out = []
@@ -92,7 +109,7 @@ def tune_threshold(ctx, atms, W, cfg, thresholds=(0.0, 1e-4, 1e-3, 1e-2, 1.0, 1e
             a.iod = thr
             a.build()
         items = [a.item() for a in atms]
-        t = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **cfg), reps)
+        t = _time(lambda: run_config(ctx, items, W, cfg, queue=queue), reps)
         ctx.check()
         errs = []
         for a, r in zip(atms, ref):
@@ -170,15 +187,20 @@ def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3, tune_iod
     cfg = tuned["best"]
     ctas = cfg["ctas"]
     queue = torch.zeros(1, dtype=torch.int32, device="cuda")
-    # sequential: one launch per atmosphere (solve only), and the whole step
-    t_seq = _time(lambda: [a.solve() for a in atms], reps)
-    t_pers = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **cfg), reps)
-    t_pers_default = _time(lambda: api.batch_solve_config(ctx, items, W, queue=queue, **tuned["default"]), reps)
+    # sequential: one launch per atmosphere (solve only, with the tuned walk), and the whole step
+    def sequential():
+        ctx.set_traversal(WALKS[cfg["walk"]])
+        for a in atms:
+            a.solve()
+        ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+    t_seq = _time(sequential, reps)
+    t_pers = _time(lambda: run_config(ctx, items, W, cfg, queue=queue), reps)
+    t_pers_default = _time(lambda: run_config(ctx, items, W, tuned["default"], queue=queue), reps)
 
     def whole_step():
         for a in atms:
             a.build()
-        api.batch_solve_config(ctx, items, W, queue=queue, **cfg)
+        run_config(ctx, items, W, cfg, queue=queue)
 
     t_step_eager = _time(whole_step, reps)
     # capture the whole step in a CUDA graph (the library calls enqueue on the capture stream)
@@ -195,7 +217,7 @@ def batch_report(scale=1.0, n_atm=24, W=8, iod=1e30, seed=None, reps=3, tune_iod
     ctx.set_stream(old)
     torch.cuda.current_stream().wait_stream(s)
     t_graph = _time(g.replay, reps)
-    done, start = api.batch_solve_config(ctx, items, W, queue=queue, timing=True, **cfg)
+    done, start = run_config(ctx, items, W, cfg, queue=queue, timing=True)
     ctx.check()
     per_atm_ms = ((done.cpu().numpy() - int(start.item())) / 1e6).tolist()
     total_dense = float(sum(dense))

@@ -939,7 +939,12 @@ static int fill_batch(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W
     if (!valid_W(W)) return fail(ctx, DEX_ERR_ARG, "batch width W must be 1, 2, 4 or 8, got %d", W);
     long long base = 0;
     max_words = 0;
+    size_t blocks_max = 0;
     P.n_atm = n_atm;
+    // the context's paired walk: work units are pairs of batches and lone batches
+    P.paired = ctx->traversal == DEX_TRAVERSAL_PAIRED ? 1 : 0;
+    P.pair_group = ctx->pair_group;
+    if (P.paired && W != 8) return fail(ctx, DEX_ERR_UNSUPPORTED, "the paired walk needs W = 8");
     for (int a = 0; a < n_atm; ++a) {
         const dex_batch_item& it = atms[a];
         if (int r = check_sparse_grid(ctx, it.nx, it.nz)) return r;
@@ -980,10 +985,13 @@ static int fill_batch(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W
         A.dirs = it.dirs;
         A.weights = it.weights;
         A.J = it.J;
-        base += (long long)((it.n_lambda + W - 1) / W) * it.capacity * parts;
+        base += (long long)dex::batch_units(P, (it.n_lambda + W - 1) / W) * it.capacity * parts;
         if ((size_t)A.n_words > max_words) max_words = (size_t)A.n_words;
-        if (max_blocks && (size_t)nb > *max_blocks) *max_blocks = (size_t)nb;
+        if ((size_t)nb > blocks_max) blocks_max = (size_t)nb;
     }
+    if (max_blocks) *max_blocks = blocks_max;
+    if (P.paired && blocks_max > (size_t)dex::kInfoMaxBlocks)
+        return fail(ctx, DEX_ERR_UNSUPPORTED, "the paired walk needs grids of at most %d blocks", dex::kInfoMaxBlocks);
     if (base > 0xffffffffLL) return fail(ctx, DEX_ERR_ARG, "too many work items");
     P.n_items = base;
     P.parts = parts;
@@ -1013,7 +1021,8 @@ static int batch_launch(dex_ctx* ctx, dex::BatchParams& P, const dex_batch_item*
                             ctx->stream);
     if (e == cudaSuccess && done_ns) e = cudaMemsetAsync(done_ns, 0, sizeof(unsigned long long) * P.n_atm, ctx->stream);
     if (e == cudaSuccess && start_ns) e = cudaMemsetAsync(start_ns, 0xff, sizeof(unsigned long long), ctx->stream);
-    const size_t smem = info ? sizeof(int) * max_blocks : sizeof(unsigned long long) * max_words;
+    // the paired walk stages one word per block (max_blocks: the largest grid)
+    const size_t smem = info || P.paired ? sizeof(int) * max_blocks : sizeof(unsigned long long) * max_words;
     if (e == cudaSuccess) e = dex::launch_batch_solve(ctx->stream, P, ctas, W, packet, info, occupancy, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch_solve launch");
     return ok(ctx);
@@ -1026,10 +1035,10 @@ int dex_batch_solve(dex_ctx* ctx, int n_atm, const dex_batch_item* atms, int W, 
     if (!queue) return fail(ctx, DEX_ERR_ARG, "queue (device scratch word) required");
     dex::BatchParams* P = new (std::nothrow) dex::BatchParams();
     if (!P) return fail(ctx, DEX_ERR_ARG, "host allocation failed");
-    size_t max_words = 0;
-    int r = fill_batch(ctx, n_atm, atms, W, *P, max_words);
+    size_t max_words = 0, max_blocks = 0;
+    int r = fill_batch(ctx, n_atm, atms, W, *P, max_words, 1, &max_blocks);
     if (!r) r = bind(ctx);
-    if (!r) r = batch_launch(ctx, *P, atms, W, ctas, max_words, queue, done_ns, start_ns);
+    if (!r) r = batch_launch(ctx, *P, atms, W, ctas, max_words, queue, done_ns, start_ns, 256, false, max_blocks);
     delete P;
     return r;
 }
@@ -1069,13 +1078,13 @@ int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms,
 {
     if (!ctx) return DEX_ERR_ARG;
     dex::BatchParams P{};  // on the stack: this call makes no allocation at all
-    size_t max_words = 0;
-    if (int r = fill_batch(ctx, n_atm, atms, W, P, max_words)) return r;
+    size_t max_words = 0, max_blocks = 0;
+    if (int r = fill_batch(ctx, n_atm, atms, W, P, max_words, 1, &max_blocks)) return r;
     if (int r = bind(ctx)) return r;
     unsigned int* scratch = nullptr;
     cudaError_t e = dex::noalloc_scratch(&scratch);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "static scratch address");
-    return batch_launch(ctx, P, atms, W, ctas, max_words, scratch, done_ns, start_ns);
+    return batch_launch(ctx, P, atms, W, ctas, max_words, scratch, done_ns, start_ns, 256, false, max_blocks);
 }
 
 }  // extern "C"
@@ -1455,6 +1464,8 @@ int dex_rc_solve(dex_ctx* ctx, int nx, int nz, int n_lambda, int W, int max_mip,
     P.n_words = (int)dex_state_words(nx, nz);
     P.cap_active = capacity;
     P.storage = storage;
+    P.paired = ctx->traversal == DEX_TRAVERSAL_PAIRED && W == 8 ? 1 : 0;
+    P.pair_group = ctx->pair_group;
     P.i_bc = i_bc;
     P.bricks = bricks;
     P.words = state_words;

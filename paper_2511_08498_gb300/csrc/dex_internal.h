@@ -81,6 +81,27 @@ __host__ __device__ inline void pair_batches(int p, int n_batch, int group, int&
     b1 = b2 = -1;
 }
 
+// Lone batches of the pairing: the middle batch of every group of odd size.
+__host__ __device__ inline int pair_lone_count(int n_batch, int group)
+{
+    const int g = pair_group_size(n_batch, group);
+    int n = 0;
+    for (int g0 = 0; g0 < n_batch; g0 += g) n += (n_batch - g0 < g ? n_batch - g0 : g) & 1;
+    return n;
+}
+__host__ __device__ inline int pair_lone_batch(int q, int n_batch, int group)
+{
+    const int g = pair_group_size(n_batch, group);
+    for (int g0 = 0; g0 < n_batch; g0 += g) {
+        const int size = n_batch - g0 < g ? n_batch - g0 : g;
+        if (size & 1) {
+            if (q == 0) return g0 + size / 2;
+            --q;
+        }
+    }
+    return -1;
+}
+
 struct HddaParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int pair_group;  // DEX_TRAVERSAL_PAIRED: batches paired within groups of this many (0: one group)
@@ -210,6 +231,8 @@ struct AtmDesc {
 struct BatchParams {
     int n_atm;
     long long n_items;
+    int paired;             // W = 8: work units are pairs of batches (pair_batches) and lone batches
+    int pair_group;         //   paired within groups of this many batches (0: one group)
     int parts;              // work items per active block and batch: 256 / probes per item
     int chunk;              // work items claimed per queue increment
     unsigned int* queue;
@@ -225,6 +248,11 @@ struct BatchParams {
 // smem_bytes: the largest table of the batch
 cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, int W, int packet, bool info,
                                bool occupancy, size_t smem_bytes);
+// work units of one atmosphere: its batches, or with P.paired its pairs and lone batches
+inline int batch_units(const BatchParams& P, int n_batch)
+{
+    return P.paired ? pair_count(n_batch, P.pair_group) + pair_lone_count(n_batch, P.pair_group) : n_batch;
+}
 cudaError_t noalloc_scratch(unsigned int** out);
 
 int chain_length(int max_mip);
@@ -271,6 +299,7 @@ struct RcParams {
     int nx, nz, nbx, nbz, n_lambda, W, n_batch, chain, n_words, cap_active, storage;
     int spacing, pnx, pnz, n_dir, level_cap;  // this cascade: probe lattice, directions, MIP cap
     int dir_fastest;                           // thread order: directions (1) or probes (0) fastest
+    int paired, pair_group;                    // W = 8: one walk per pair of batches (pair_batches)
     float t_s, t_e, i_bc;                      // radiance interval, boundary intensity
     const float* bricks;
     const unsigned long long* words;

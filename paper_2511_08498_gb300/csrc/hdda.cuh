@@ -89,6 +89,38 @@ __device__ __forceinline__ auto model_load(const typename Model::Params&, const 
     return Model::load(p);
 }
 
+// Two batches' records of one voxel, `off` floats apart, in format ST: the
+// wavelengths of the first are 0..7 of the walk, those of the second 8..15 (a
+// walk shared by a pair of batches on their common levels).  Empty blocks are
+// stepped over without a record (the zero record has no second batch beside it).
+template <int ST, int MINB>
+struct PairRecModel {
+    static constexpr int kStride = RecFmt<8, ST>::kStride;
+    static constexpr bool kPerBatch = true;
+    static constexpr int kMinBlocks = MINB;
+    static constexpr bool kEarlyLoad = ST == kStoreF32;
+    static constexpr bool kZeroNoop = false;
+    struct Params {
+        long long off;
+    };
+    struct Voxel {
+        Record<8> a, b;
+    };
+    __device__ __forceinline__ static Voxel load(const Params& M, const float* p)
+    {
+        Voxel v;
+        v.a = RecFmt<8, ST>::load(p);
+        v.b = RecFmt<8, ST>::load(p + M.off);
+        return v;
+    }
+    __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
+                                                     float* I, float* T)
+    {
+        segments<8>(v.a.S, v.a.chi, nl2, I, T);
+        segments<8>(v.b.S, v.b.chi, nl2, I + 8, T + 8);
+    }
+};
+
 // Voxel models: Model::kStride floats per voxel record, Model::kPerBatch whether
 // records differ per wavelength batch, Model::kEarlyLoad whether the record is
 // loaded at the top of each step, Model::kZeroNoop whether a record of zeros

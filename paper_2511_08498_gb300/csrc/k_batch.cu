@@ -54,11 +54,14 @@ struct StaticRec {
 // block (offset * 8 + state); otherwise the packed 3-bit state words.  Every
 // probe accumulates J over all directions in its thread, in the order of the
 // single-grid solve, so results do not depend on these choices.
-template <int W, int NT, bool kInfo, int kMinCtas>
+// kPair (W = 8): a work unit is a pair of batches (pair_batches) walked once on
+// the smaller of their two levels, 16 wavelengths per thread, or a lone batch
+// (pair_lone_batch) walked alone, as dex_formal_solve_hdda's paired walk.
+template <int W, int NT, bool kInfo, int kMinCtas, bool kPair = false>
 __global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams P)
 {
     extern __shared__ unsigned long long s_dyn[];
-    __shared__ float s_J[W][NT];
+    __shared__ float s_J[kPair ? 2 * W : W][NT];
     __shared__ float s_dx[DEX_MAX_DIRS], s_dz[DEX_MAX_DIRS], s_w[DEX_MAX_DIRS];
     __shared__ unsigned int s_item;
     constexpr int kParts = 256 / NT;
@@ -86,9 +89,23 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams 
             const int part = (int)(local % kParts);
             const int b = (int)(unit / A.cap_active), r = (int)(unit % A.cap_active);
             if (r >= *A.n_active) continue;
+            // kPair: b numbers the atmosphere's pairs, then its lone batches
+            int b1 = b, b2 = -1;
+            if constexpr (kPair) {
+                const int n_batch = (A.n_lambda + W - 1) / W, np = pair_count(n_batch, P.pair_group);
+                if (b < np) pair_batches(b, n_batch, P.pair_group, b1, b2);
+                else b1 = pair_lone_batch(b - np, n_batch, P.pair_group);
+            }
             __syncthreads();  // every thread is done with the previous item's shared data
             if (a != cur_atm || b != cur_batch) {
-                if constexpr (kInfo) {
+                if constexpr (kPair) {
+                    // one word per block, offset * 8 + the smaller of the pair's states
+                    const int nb = A.nbx * A.nbz;
+                    const unsigned long long* w1 = A.words + (size_t)b1 * A.n_words;
+                    const unsigned long long* w2 = A.words + (size_t)(b2 >= 0 ? b2 : b1) * A.n_words;
+                    for (int q = tid; q < nb; q += NT)
+                        s_info[q] = pack_block_info(A.block_offset[q], min(block_state(w1, q), block_state(w2, q)));
+                } else if constexpr (kInfo) {
                     const int nb = A.nbx * A.nbz;
                     const unsigned long long* wb = A.words + (size_t)b * A.n_words;
                     for (int q = tid; q < nb; q += NT) s_info[q] = pack_block_info(A.block_offset[q], block_state(wb, q));
@@ -105,7 +122,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams 
                 cur_batch = b;
             }
 #pragma unroll
-            for (int w = 0; w < W; ++w) s_J[w][tid] = 0.0f;
+            for (int w = 0; w < (kPair ? 2 * W : W); ++w) s_J[w][tid] = 0.0f;
             __syncthreads();
 
             const int blk0 = A.active[r];
@@ -113,7 +130,7 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams 
             const int wrp = tid >> 5;
             const int i = bx0 * DEX_BLOCK + (wrp & 1) * 8 + (tid & 7);
             const int j = bz0 * DEX_BLOCK + part * (DEX_BLOCK / kParts) + (wrp >> 1) * 4 + ((tid & 31) >> 3);
-            const int state0 = (kInfo ? (s_info[blk0] & 7) : block_state(s_dyn, blk0)) - 1;
+            const int state0 = (kInfo || kPair ? (s_info[blk0] & 7) : block_state(s_dyn, blk0)) - 1;
             if (state0 < 0) {
                 capped = true;
                 continue;
@@ -125,31 +142,46 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams 
             G.nbz = A.nbz;
             G.chain = A.chain;
             G.cap_active = A.cap_active;
-            G.batch_base = A.bricks + (size_t)b * A.cap_active * A.chain * (2 * W);
+            const size_t batch_floats = (size_t)A.cap_active * A.chain * (2 * W);
+            G.batch_base = A.bricks + (size_t)b1 * batch_floats;
             set_box_full(G);
 #pragma unroll
             for (int q = 0; q < 4; ++q) G.band[q] = A.band[q];
             const int mip0 = min(state0, distance_cap(G, 0.0f));
             typename StaticRec<W>::Params M{};
             for (int k = 0; k < A.n_dir; ++k) {
-                float I[W], T[W];
-#pragma unroll
-                for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
-                if constexpr (kInfo)
-                    trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
-                                                       InfoLookup{s_info}, I, T, nseg_unused, capped);
-                else
-                    trace_ray<W, false, StaticRec<W>>(G, M, b, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
-                                                       WordLookup{s_dyn, A.block_offset}, I, T, nseg_unused, capped);
                 const float wk = s_w[k];
+                if (kPair && b2 >= 0) {
+                    // the pair: 16 wavelengths along one walk
+                    using PM = PairRecModel<kStoreF32, kMinCtas>;
+                    const typename PM::Params M2{(long long)(b2 - b1) * (long long)batch_floats};
+                    float I[2 * W], T[2 * W];
 #pragma unroll
-                for (int w = 0; w < W; ++w) s_J[w][tid] = fmaf(wk, fmaf(T[w], A.i_bc, I[w]), s_J[w][tid]);
+                    for (int w = 0; w < 2 * W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
+                    trace_ray<2 * W, false, PM>(G, M2, b1, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
+                                                InfoLookup{s_info}, I, T, nseg_unused, capped);
+#pragma unroll
+                    for (int w = 0; w < 2 * W; ++w) s_J[w][tid] = fmaf(wk, fmaf(T[w], A.i_bc, I[w]), s_J[w][tid]);
+                } else {
+                    float I[W], T[W];
+#pragma unroll
+                    for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
+                    if constexpr (kInfo || kPair)
+                        trace_ray<W, false, StaticRec<W>>(G, M, b1, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
+                                                           InfoLookup{s_info}, I, T, nseg_unused, capped);
+                    else
+                        trace_ray<W, false, StaticRec<W>>(G, M, b1, i, j, bx0, bz0, r, mip0, s_dx[k], s_dz[k],
+                                                           WordLookup{s_dyn, A.block_offset}, I, T, nseg_unused,
+                                                           capped);
+#pragma unroll
+                    for (int w = 0; w < W; ++w) s_J[w][tid] = fmaf(wk, fmaf(T[w], A.i_bc, I[w]), s_J[w][tid]);
+                }
             }
             const long long n_cells = (long long)A.nx * A.nz;
 #pragma unroll
-            for (int w = 0; w < W; ++w) {
-                const int l = b * W + w;
-                if (l < A.n_lambda) A.J[(size_t)l * n_cells + (size_t)j * A.nx + i] = s_J[w][tid];
+            for (int w = 0; w < (kPair ? 2 * W : W); ++w) {
+                const int l = w < W ? b1 * W + w : b2 * W + (w - W);
+                if ((w < W || b2 >= 0) && l < A.n_lambda) A.J[(size_t)l * n_cells + (size_t)j * A.nx + i] = s_J[w][tid];
             }
             if (P.done_ns != nullptr) {
                 __syncthreads();
@@ -160,10 +192,10 @@ __global__ void __launch_bounds__(NT, kMinCtas) k_batch_solve(const BatchParams 
     if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
 }
 
-template <int W, int NT, bool kInfo, int kMinCtas>
+template <int W, int NT, bool kInfo, int kMinCtas, bool kPair = false>
 cudaError_t launch_batch_t(cudaStream_t s, const BatchParams& P, int ctas, size_t smem)
 {
-    auto kernel = k_batch_solve<W, NT, kInfo, kMinCtas>;
+    auto kernel = k_batch_solve<W, NT, kInfo, kMinCtas, kPair>;
     if (smem > 16 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -208,6 +240,19 @@ cudaError_t launch_batch_solve(cudaStream_t s, const BatchParams& P, int ctas, i
     cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess || P.n_items == 0) return e;
     if (occupancy && W != 8) return cudaErrorInvalidValue;
+    if (P.paired) {
+        // pairs of batches (W = 8): one word per block staged, the compiler's budget
+        // bounded at 128 registers (two 256-thread CTAs per SM)
+        if (W != 8) return cudaErrorInvalidValue;
+        switch (packet) {
+            case 256: e = launch_batch_t<8, 256, true, 2, true>(s, P, ctas, smem_bytes); break;
+            case 128: e = launch_batch_t<8, 128, true, 4, true>(s, P, ctas, smem_bytes); break;
+            case 64: e = launch_batch_t<8, 64, true, 8, true>(s, P, ctas, smem_bytes); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     switch (W) {
         case 1: e = launch_batch_w<1, false>(s, P, ctas, packet, info, smem_bytes); break;
         case 2: e = launch_batch_w<2, false>(s, P, ctas, packet, info, smem_bytes); break;

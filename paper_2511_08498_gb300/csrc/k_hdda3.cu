@@ -332,11 +332,8 @@ cudaError_t launch_solve_hdda3(cudaStream_t s, const Hdda3Params& P0)
         }
         // the middle batch of every group of odd size alone, by the per-batch walk
         // on a view of that batch
-        const int g = pair_group_size(P.n_batch, P.pair_group);
-        for (int g0 = 0; g0 < P.n_batch; g0 += g) {
-            const int size = min(g, P.n_batch - g0);
-            if (size % 2 == 0) continue;
-            const int m = g0 + size / 2;
+        for (int q = 0; q < pair_lone_count(P.n_batch, P.pair_group); ++q) {
+            const int m = pair_lone_batch(q, P.n_batch, P.pair_group);
             Hdda3Params Q = P0;
             Q.traversal = DEX_TRAVERSAL_PER_BATCH;
             Q.n_batch = 1;

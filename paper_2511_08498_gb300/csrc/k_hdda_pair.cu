@@ -26,58 +26,43 @@ namespace dex {
 
 namespace {
 
-// The pair's state (16 intensities and transmissions, two records loaded at the
-// top of each step) takes about 120 registers: 2 CTAs of 256 threads per SM.
-// Measured on the 1024^2 static-line solve against this configuration (records
-// loaded early, the step loop unrolled four times): the loop unrolled twice or
-// not at all +1.4%, records loaded after the stepping +3.7%; a 3-CTA register
-// budget spills and is 70% slower.
-constexpr int kPairMinBlocks = 2;
-
-// Two batches' records of one voxel, `off` floats apart, in format ST; the
-// wavelengths of the first are 0..7 of the walk, those of the second 8..15.
+// Launch shape per brick format.  The pair's state (16 intensities and
+// transmissions, two records loaded at the top of each step) takes about 120
+// registers with float32 records: 2 CTAs of 256 threads per SM.  Bfloat16
+// records hold half the registers and run at 5 CTAs of 128 threads (at most 102
+// registers).  Measured on the 1024^2 static-line solve (IoD 1e-2 / unlimited
+// averaging):
+//   float32, 256 threads, 2 CTAs (this)         173.6 / 62.8 ms
+//   float32, 128 threads, 5 CTAs (96 registers)  176.4 / 66.1 ms
+//   float32, 128 threads, 4 CTAs                 173.8 / 66.0 ms
+//   float32, 256 threads, 3 CTAs (80, spills)    294.4 / 106.1 ms
+//   bfloat16, 128 threads, 5 CTAs (this)         165.0 / 66.2 ms
+//   bfloat16, 256 threads, 2 CTAs                171.5 / 66.6 ms
+//   bfloat16, 128 threads, 6 CTAs (80 registers) 174.3 / 69.8 ms
+// and, for float32 at 256 threads, the step loop unrolled twice or not at all
+// +1.4%, records loaded after the stepping +3.7%.
 template <int ST>
-struct PairModel {
-    static constexpr int kStride = RecFmt<8, ST>::kStride;
-    static constexpr bool kPerBatch = true;
-    static constexpr int kMinBlocks = kPairMinBlocks;
-    static constexpr bool kEarlyLoad = ST == kStoreF32;
-    // empty blocks are stepped over without a record (the zero record has no
-    // second batch beside it)
-    static constexpr bool kZeroNoop = false;
-    struct Params {
-        long long off;
-    };
-    struct Voxel {
-        Record<8> a, b;
-    };
-    __device__ __forceinline__ static Voxel load(const Params& M, const float* p)
-    {
-        Voxel v;
-        v.a = RecFmt<8, ST>::load(p);
-        v.b = RecFmt<8, ST>::load(p + M.off);
-        return v;
-    }
-    __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
-                                                     float* I, float* T)
-    {
-        segments<8>(v.a.S, v.a.chi, nl2, I, T);
-        segments<8>(v.b.S, v.b.chi, nl2, I + 8, T + 8);
-    }
-};
+constexpr int pair_threads() { return ST == kStoreBF16 ? 128 : 256; }
+template <int ST>
+constexpr int pair_min_blocks() { return ST == kStoreBF16 ? 5 : 2; }
+// probes per CTA: 16 x (threads / 16) rows of a block; CTAs per active block and pair
+template <int ST>
+constexpr int pair_parts() { return DEX_BLOCK * DEX_BLOCK / pair_threads<ST>(); }
 
-// grid (cap_active, pair_count pairs), 256 threads; dynamic shared memory one
-// word per block: offset * 8 + the pair's minimum state
+template <int ST>
+using PairModel = PairRecModel<ST, pair_min_blocks<ST>()>;
+
 // EXT: each probe's own-voxel emission is left out (the first segment of every
 // ray, as k_solve_hdda_t with EXT).
 template <int ST, bool COUNT, bool EXT>
-__global__ void __launch_bounds__(256, kPairMinBlocks) k_solve_hdda_pair(const HddaParams P)
+__global__ void __launch_bounds__(pair_threads<ST>(), pair_min_blocks<ST>()) k_solve_hdda_pair(const HddaParams P)
 {
     using Model = PairModel<ST>;
+    constexpr int kParts = pair_parts<ST>();
     extern __shared__ int s_info[];
-    __shared__ float s_J[16][256];
+    __shared__ float s_J[16][pair_threads<ST>()];
     __shared__ int s_box[4];
-    const int a0 = blockIdx.x;
+    const int a0 = blockIdx.x / kParts, part = blockIdx.x - a0 * kParts;
     if (a0 >= *P.n_active) return;
     int b1, b2;
     pair_batches(blockIdx.y, P.n_batch, P.pair_group, b1, b2);
@@ -118,10 +103,11 @@ __global__ void __launch_bounds__(256, kPairMinBlocks) k_solve_hdda_pair(const H
 
     const int blk0 = P.active[a0];
     const int bx0 = blk0 % P.nbx, bz0 = blk0 / P.nbx;
-    // warp w covers an 8 x 4 tile of the block (as in k_solve_hdda_t)
+    // the CTA's probes: rows part * (16 / kParts) .. of the block; warp w covers an
+    // 8 x 4 tile of them (as in k_solve_hdda_t)
     const int wrp = tid >> 5;
     const int i = bx0 * DEX_BLOCK + (wrp & 1) * 8 + (tid & 7);
-    const int j = bz0 * DEX_BLOCK + (wrp >> 1) * 4 + ((tid & 31) >> 3);
+    const int j = bz0 * DEX_BLOCK + part * (DEX_BLOCK / kParts) + (wrp >> 1) * 4 + ((tid & 31) >> 3);
     const int state0 = (s_info[blk0] & 7) - 1;
     if (state0 < 0) {  // state words do not describe this active block
         raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
@@ -181,14 +167,14 @@ template <int ST>
 cudaError_t launch_pair(cudaStream_t s, const HddaParams& P)
 {
     const size_t smem = sizeof(int) * (size_t)P.nbx * P.nbz;
-    dim3 grid((unsigned)P.cap_active, (unsigned)pair_count(P.n_batch, P.pair_group));
+    dim3 grid((unsigned)(P.cap_active * pair_parts<ST>()), (unsigned)pair_count(P.n_batch, P.pair_group));
     auto kernel = P.exclude_own ? (P.seg_count ? k_solve_hdda_pair<ST, true, true> : k_solve_hdda_pair<ST, false, true>)
                                 : (P.seg_count ? k_solve_hdda_pair<ST, true, false> : k_solve_hdda_pair<ST, false, false>);
     if (smem > 24 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kernel<<<grid, 256, smem, s>>>(P);
+    kernel<<<grid, pair_threads<ST>(), smem, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -216,11 +202,8 @@ cudaError_t launch_solve_hdda_paired(cudaStream_t s, const HddaParams& P)
     }
     // the middle batch of every group of odd size alone, by the per-batch walk on
     // a view of that batch
-    const int g = pair_group_size(P.n_batch, P.pair_group);
-    for (int g0 = 0; g0 < P.n_batch; g0 += g) {
-        const int size = min(g, P.n_batch - g0);
-        if (size % 2 == 0) continue;
-        const int m = g0 + size / 2;
+    for (int q = 0; q < pair_lone_count(P.n_batch, P.pair_group); ++q) {
+        const int m = pair_lone_batch(q, P.n_batch, P.pair_group);
         HddaParams Q = P;
         Q.traversal = DEX_TRAVERSAL_PER_BATCH;
         Q.n_batch = 1;

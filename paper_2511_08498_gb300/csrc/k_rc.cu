@@ -35,12 +35,24 @@ __device__ __forceinline__ int rc_block_state(const unsigned long long* words, i
     return (int)((words[wi] >> sh) & 7ull);
 }
 
+// Block state of the walk: NB = 1 the batch's own, NB = 2 the smaller of the
+// two batches' states (0 = empty wins).
+template <int NB>
+__device__ __forceinline__ int rc_walk_state(const unsigned long long* w1, const unsigned long long* w2, int blk)
+{
+    const int s1 = rc_block_state(w1, blk);
+    return NB == 2 ? min(s1, rc_block_state(w2, blk)) : s1;
+}
+
 // Emission I and transmission T of the interval [t_s, t_e] of the ray o + t d
 // through the sparse mipmapped grid; returns true when the ray leaves the grid
-// before t_e.
-template <int W, bool COUNT, int ST>
-__device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __restrict__ base,
-                                            const unsigned long long* __restrict__ words, float ox, float oz,
+// before t_e.  NB = 2: two wavelength batches (bricks `off` floats apart, state
+// words words2) along one walk on the smaller of their levels; I and T hold
+// 2 W values, the second batch's from index W.
+template <int W, bool COUNT, int ST, int NB = 1>
+__device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __restrict__ base, long long off,
+                                            const unsigned long long* __restrict__ words,
+                                            const unsigned long long* __restrict__ words2, float ox, float oz,
                                             float dx, float dz, float* I, float* T, unsigned int& nseg,
                                             bool& capped)
 {
@@ -59,7 +71,7 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
     const int cz = min(max(__float2int_rd(fmaf(P.t_s, dz, oz)), 0), P.nz - 1);
     int bxc = cx >> 4, bzc = cz >> 4;
     int blk = bzc * P.nbx + bxc;
-    int st = rc_block_state(words, blk) - 1;
+    int st = rc_walk_state<NB>(words, words2, blk) - 1;
     int mip = st < 0 ? -1 : min(st, P.level_cap);
     int shift = mip >= 0 ? mip : 4;
     int vox = 1 << shift, side = DEX_BLOCK >> shift;
@@ -71,11 +83,14 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
         rp = base + ((size_t)P.block_offset[blk] * P.chain + rc_level_offset(mip) + lz * side + lx) * REC;
     float th_prev = P.t_s, tl_prev = 0.0f;
 
-    Record<W> r;
+    Record<W> r, r2;
     for (int it = 0;; ++it) {
         // the current voxel's record is issued first: the stepping and crossing
         // bookkeeping below hides its latency
-        if (mip >= 0) r = RecFmt<W, ST>::load(rp);
+        if (mip >= 0) {
+            r = RecFmt<W, ST>::load(rp);
+            if constexpr (NB == 2) r2 = RecFmt<W, ST>::load(rp + off);
+        }
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
         float th = on_x ? tnx : tnz;
@@ -102,7 +117,7 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
                 rp += negz ? -side * REC : side * REC;
                 cross = (unsigned)lz >= (unsigned)side;
             }
-            if (cross && all_opaque<W>(T)) break;  // the rest adds exact zeros
+            if (cross && all_opaque<NB * W>(T)) break;  // the rest adds exact zeros
             if (cross) {
                 const int bxn = bxc + (on_x ? sx : 0), bzn = bzc + (on_x ? 0 : sz);
                 if ((unsigned)bxn >= (unsigned)P.nbx || (unsigned)bzn >= (unsigned)P.nbz) {
@@ -110,7 +125,7 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
                     break;
                 }
                 blk = bzn * P.nbx + bxn;
-                st = rc_block_state(words, blk) - 1;
+                st = rc_walk_state<NB>(words, words2, blk) - 1;
                 const int mip_new = st < 0 ? -1 : min(st, P.level_cap);
                 if (mip_new == mip) {
                     if (on_x) lx = negx ? side - 1 : 0;
@@ -146,7 +161,8 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
         }
         if (cur_mip >= 0) {
             segments<W>(r.S, r.chi, len * kNegLog2e, I, T);
-            if (COUNT) nseg += (th > th_prev);
+            if constexpr (NB == 2) segments<W>(r2.S, r2.chi, len * kNegLog2e, I + W, T + W);
+            if (COUNT) nseg += NB * (th > th_prev);
         }
         if (last) break;
         th_prev = th;
@@ -155,10 +171,15 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
     return left;
 }
 
-template <int W, bool COUNT, int ST>
-__global__ void __launch_bounds__(256, 4) k_rc_cascade(const RcParams P)
+// NB = 1: blockIdx.y is the batch (with P.paired: the lone batch
+// pair_lone_batch(blockIdx.y)); NB = 2: the pair pair_batches(blockIdx.y), one
+// walk for both batches on the smaller of their levels.
+template <int W, bool COUNT, int ST, int NB>
+__global__ void __launch_bounds__(256, NB == 1 ? 4 : 2) k_rc_cascade(const RcParams P)
 {
-    const int b = blockIdx.y;
+    int b = blockIdx.y, b2 = blockIdx.y;
+    if constexpr (NB == 2) pair_batches(blockIdx.y, P.n_batch, P.pair_group, b, b2);
+    else if (P.paired) b = b2 = pair_lone_batch(blockIdx.y, P.n_batch, P.pair_group);
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n_probe = (long long)P.pnx * P.pnz;
     if (g >= n_probe * P.n_dir) return;
@@ -172,20 +193,26 @@ __global__ void __launch_bounds__(256, 4) k_rc_cascade(const RcParams P)
     }
     const int px = p % P.pnx, pz = p / P.pnx;
     const unsigned long long* words = P.words + (size_t)b * P.n_words;
+    const unsigned long long* words2 = P.words + (size_t)b2 * P.n_words;
     if (P.spacing == 1) {  // cascade 0: probes only in non-empty blocks
         if (rc_block_state(words, (pz >> 4) * P.nbx + (px >> 4)) == 0) return;
     }
     constexpr int REC = RecFmt<W, ST>::kStride;
-    const float* base = P.bricks + (size_t)b * P.cap_active * P.chain * REC;
+    const size_t batch_floats = (size_t)P.cap_active * P.chain * REC;
+    const float* base = P.bricks + (size_t)b * batch_floats;
+    const long long off = (long long)(b2 - b) * (long long)batch_floats;
     const float ox = (float)P.spacing * ((float)px + 0.5f), oz = (float)P.spacing * ((float)pz + 0.5f);
     const float dx = P.dirs[2 * k], dz = P.dirs[2 * k + 1];
-    float I[W], T[W];
+    float I[NB * W], T[NB * W];
 #pragma unroll
-    for (int w = 0; w < W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
+    for (int w = 0; w < NB * W; ++w) { I[w] = 0.0f; T[w] = 1.0f; }
     unsigned int nseg = 0;
     bool capped = false;
-    const bool left = rc_interval<W, COUNT, ST>(P, base, words, ox, oz, dx, dz, I, T, nseg, capped);
+    const bool left = rc_interval<W, COUNT, ST, NB>(P, base, off, words, words2, ox, oz, dx, dz, I, T, nseg, capped);
 
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+    const int bq = q == 0 ? b : b2;
     float R[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) R[w] = P.i_bc;
@@ -198,7 +225,7 @@ __global__ void __launch_bounds__(256, 4) k_rc_cascade(const RcParams P)
         const int xa = min(max(x0, 0), qnx - 1), xb = min(max(x0 + 1, 0), qnx - 1);
         const int za = min(max(z0, 0), qnz - 1), zb = min(max(z0 + 1, 0), qnz - 1);
         const long long q_probe = (long long)qnx * qnz;
-        const float* up = P.upper + (size_t)b * (size_t)(4 * P.n_dir) * q_probe * W;
+        const float* up = P.upper + (size_t)bq * (size_t)(4 * P.n_dir) * q_probe * W;
         const int qs[4] = {za * qnx + xa, za * qnx + xb, zb * qnx + xa, zb * qnx + xb};
         const float ws[4] = {(1.0f - fz) * (1.0f - fx), (1.0f - fz) * fx, fz * (1.0f - fx), fz * fx};
 #pragma unroll
@@ -218,9 +245,10 @@ __global__ void __launch_bounds__(256, 4) k_rc_cascade(const RcParams P)
             for (int w = 0; w < W; ++w) R[w] = fmaf(ws[c] * 0.25f, m[w], R[w]);
         }
     }
-    float* dst = P.out + ((size_t)b * (size_t)P.n_dir * n_probe + (size_t)k * n_probe + p) * W;
+    float* dst = P.out + ((size_t)bq * (size_t)P.n_dir * n_probe + (size_t)k * n_probe + p) * W;
 #pragma unroll
-    for (int w = 0; w < W; ++w) dst[w] = fmaf(T[w], R[w], I[w]);
+    for (int w = 0; w < W; ++w) dst[w] = fmaf(T[q * W + w], R[w], I[q * W + w]);
+    }
     if (capped) raise_status(P.status, DEX_ERR_TRAVERSAL_CAP);
     if (COUNT && P.seg_count != nullptr) atomicAdd(P.seg_count, (unsigned long long)nseg);
 }
@@ -251,13 +279,28 @@ __global__ void __launch_bounds__(256) k_rc_mean(const RcParams P, const float* 
     }
 }
 
+template <int W, int ST, int NB>
+void launch_rc_nb(cudaStream_t s, const RcParams& P, int n_units)
+{
+    if (n_units == 0) return;
+    const long long n = (long long)P.pnx * P.pnz * P.n_dir;
+    const dim3 grid((unsigned)((n + 255) / 256), (unsigned)n_units);
+    if (P.seg_count) k_rc_cascade<W, true, ST, NB><<<grid, 256, 0, s>>>(P);
+    else k_rc_cascade<W, false, ST, NB><<<grid, 256, 0, s>>>(P);
+}
+
 template <int W, int ST>
 void launch_rc_w(cudaStream_t s, const RcParams& P)
 {
-    const long long n = (long long)P.pnx * P.pnz * P.n_dir;
-    const dim3 grid((unsigned)((n + 255) / 256), (unsigned)P.n_batch);
-    if (P.seg_count) k_rc_cascade<W, true, ST><<<grid, 256, 0, s>>>(P);
-    else k_rc_cascade<W, false, ST><<<grid, 256, 0, s>>>(P);
+    if constexpr (W == 8) {
+        if (P.paired) {
+            // pairs of batches on one walk each, then the lone batches
+            launch_rc_nb<8, ST, 2>(s, P, pair_count(P.n_batch, P.pair_group));
+            launch_rc_nb<8, ST, 1>(s, P, pair_lone_count(P.n_batch, P.pair_group));
+            return;
+        }
+    }
+    launch_rc_nb<W, ST, 1>(s, P, P.n_batch);
 }
 
 }  // namespace

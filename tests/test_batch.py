@@ -89,3 +89,36 @@ def test_configuration_is_checked():
     for bad in (dict(packet=96), dict(chunk=0), dict(chunk=65), dict(staging=2), dict(occupancy=3)):
         with pytest.raises(api.DexError):
             api.batch_solve_config(ctx, items, 8, **bad)
+
+
+# the paired walk (DEX_TRAVERSAL_PAIRED): work units are the pairs of batches and
+# the lone batches; 16, 24 and 8 wavelengths give one pair, one pair and a lone
+# batch, and a lone batch; pair group 2 pairs 0-1 of the 24-wavelength atmosphere
+# and leaves batch 2 alone
+@pytest.mark.parametrize("cfg,group", [(dict(ctas=0, packet=256, chunk=1, staging=0, occupancy=0), 0),
+                                       (dict(ctas=7, packet=128, chunk=3, staging=1, occupancy=1), 0),
+                                       (dict(ctas=0, packet=64, chunk=2, staging=0, occupancy=0), 2)])
+def test_paired_batch_equals_per_atmosphere_paired_solves(cfg, group):
+    from paper_2511_08498_gb300 import api
+    ctx = api.Context(0)
+    atms = build_atmospheres(ctx, SPECS)
+    ctx.set_traversal(api.TRAVERSAL_PAIRED)
+    ctx.set_pair_group(group)
+    try:
+        refs = []
+        for a in atms:
+            J, _, _ = api.formal_solve_hdda(ctx, a["grid"], a["mips"], a["dirs"], a["w"], band=a["band"])
+            refs.append(J.clone())
+        items = [api.batch_item(a["grid"], a["mips"], a["dirs_dev"], a["w_dev"], a["J"], band=a["band"])
+                 for a in atms]
+        for a in atms:
+            a["J"].fill_(-1.0)
+        done, start = api.batch_solve_config(ctx, items, 8, timing=True, **cfg)
+        ctx.check()
+    finally:
+        ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+        ctx.set_pair_group(0)
+    for a, r in zip(atms, refs):
+        assert torch.equal(a["J"], r), cfg
+    d = done.cpu().numpy()
+    assert (d > 0).all() and (d >= int(start.item())).all()
