@@ -245,7 +245,8 @@ size_t dex_state_words(int nx, int nz);
 int dex_chain_voxels(int max_mip);
 
 /* Record storage formats of the static bricks (accumulation along rays is float32 in all):
- *   DEX_STORE_F32  : S[W], chi[W] float32                       (2W floats per record)
+ *   DEX_STORE_F32  : S[W], chi[W] float32 (2W floats per voxel), stored per brick row:
+ *                    the S[W] of the row's voxels in x order, then their chi[W]
  *   DEX_STORE_BF16 : S[W], chi[W] bfloat16, round to nearest    (W floats; W = 4 or 8)
  *   DEX_STORE_F16  : float32 max S, max chi, 2 pad words, then S / max S and chi / max chi
  *                    as float16, round to nearest (4 + W floats; W = 4 or 8).  Values
@@ -281,8 +282,12 @@ typedef struct {
  *   level_cap         device [nbz * nbx] per-block upper bound on the level, or NULL
  *   bricks            device [n_batch][capacity][chain][record] output records (format
  *                     params->storage; alignment as for the planes above):
- *                     level m of a block starts at record sum_{k<m} (16 >> k)^2 and
- *                     is row-major over its (16 >> m)^2 voxels
+ *                     level m of a block starts at voxel sum_{k<m} (16 >> k)^2 and
+ *                     is row-major over its (16 >> m)^2 voxels; in float32 each row of
+ *                     side = 16 >> m voxels is S of voxels 0..side-1 (W floats each),
+ *                     then chi of them (a warp's rays at neighbouring voxels of a row
+ *                     then read contiguous runs); the other formats store one record
+ *                     per voxel
  *   state_words       device [n_batch][dex_state_words] output (zeroed by the call):
  *                     block k's state (0 = empty, level + 1) in word k / 21, bits 3 (k % 21)
  * The level of a block is the largest m <= max_mip such that every 2x2 group of

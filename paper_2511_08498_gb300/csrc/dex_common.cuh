@@ -362,6 +362,68 @@ struct RecFmt<W, kStoreF16> {
     }
 };
 
+// Layout of the 2D sparse grids' MIP bricks.  Level m of a block is side x side
+// voxels (side = 16 >> m) stored row by row (z outer, x inner).  In float32 a
+// row holds the S values of its voxels (W floats each, in x order) and then
+// their chi values: rays of a warp at neighbouring voxels of a row read one
+// contiguous run of S and one of chi, so a 256-bit warp load touches half as
+// many 128-byte lines as with S and chi side by side per voxel (ncu on the
+// 512^2 paired walk: L1 load wavefronts -30% for the same sectors).  The
+// reduced-precision formats, whose records are 32 or 48 bytes, keep one record
+// per voxel.
+template <int W, int ST>
+struct BrickFmt {
+    static constexpr bool kSplit = ST == kStoreF32;
+    static constexpr int kRec = RecFmt<W, ST>::kStride;  // floats per voxel
+    static constexpr int kX = kSplit ? W : kRec;         // floats between x neighbours of a row
+    // offset (floats) of voxel (lx, lz) of a level of `side` voxels per row whose
+    // first voxel is voxel `first` of the brick array
+    __host__ __device__ __forceinline__ static long long offset(long long first, int lz, int lx, int side)
+    {
+        return (first + (long long)lz * side) * kRec + (long long)lx * kX;
+    }
+    // floats from a voxel's S to its chi (0: a record holds both)
+    __host__ __device__ __forceinline__ static int chi_off(int side) { return kSplit ? side * W : 0; }
+    __device__ __forceinline__ static Record<W> load(const float* p, int coff)
+    {
+        if constexpr (kSplit) {
+            Record<W> r;
+            if constexpr (W == 8) {  // 32-byte aligned runs
+                ldg256(p, r.S);
+                ldg256(p + coff, r.chi);
+            } else if constexpr (W == 4) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+                const float4 c = __ldg(reinterpret_cast<const float4*>(p + coff));
+                r.S[0] = a.x; r.S[1] = a.y; r.S[2] = a.z; r.S[3] = a.w;
+                r.chi[0] = c.x; r.chi[1] = c.y; r.chi[2] = c.z; r.chi[3] = c.w;
+            } else if constexpr (W == 2) {
+                const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+                const float2 c = __ldg(reinterpret_cast<const float2*>(p + coff));
+                r.S[0] = a.x; r.S[1] = a.y;
+                r.chi[0] = c.x; r.chi[1] = c.y;
+            } else {
+                r.S[0] = __ldg(p);
+                r.chi[0] = __ldg(p + coff);
+            }
+            return r;
+        } else {
+            return RecFmt<W, ST>::load(p);
+        }
+    }
+    __device__ __forceinline__ static void store(float* p, int coff, const float* S, const float* chi)
+    {
+        if constexpr (kSplit) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) {
+                p[w] = S[w];
+                p[coff + w] = chi[w];
+            }
+        } else {
+            RecFmt<W, ST>::store(p, S, chi);
+        }
+    }
+};
+
 // Quadrature passed by value to the solve kernels.
 struct Quadrature {
     int n_dir;

@@ -74,6 +74,21 @@ namespace {
 __device__ __align__(32) float g_zero_record[32] = {0.0f};
 }  // namespace
 
+// Voxel models whose records are float32 brick rows (BrickFmt: a row's S
+// values, then its chi values) declare kSplit = true, the floats between x
+// neighbours of a row as kSplitStride, and load the record of a voxel from its
+// S pointer and the distance to its chi (Model::load_split).
+template <class M, class = void>
+struct SplitOf {
+    static constexpr bool value = false;
+    static constexpr int stride = 0;
+};
+template <class M>
+struct SplitOf<M, decltype((void)M::kSplit)> {
+    static constexpr bool value = M::kSplit;
+    static constexpr int stride = M::kSplitStride;
+};
+
 // Record load of a voxel model: Model::load(M, p) where the model declares it
 // (its records need the launch parameters, e.g. a second batch's offset),
 // Model::load(p) otherwise.
@@ -96,6 +111,8 @@ __device__ __forceinline__ auto model_load(const typename Model::Params&, const 
 template <int ST, int MINB>
 struct PairRecModel {
     static constexpr int kStride = RecFmt<8, ST>::kStride;
+    static constexpr bool kSplit = BrickFmt<8, ST>::kSplit;
+    static constexpr int kSplitStride = BrickFmt<8, ST>::kX;
     static constexpr bool kPerBatch = true;
     static constexpr int kMinBlocks = MINB;
     static constexpr bool kEarlyLoad = ST == kStoreF32;
@@ -111,6 +128,13 @@ struct PairRecModel {
         Voxel v;
         v.a = RecFmt<8, ST>::load(p);
         v.b = RecFmt<8, ST>::load(p + M.off);
+        return v;
+    }
+    __device__ __forceinline__ static Voxel load_split(const Params& M, const float* p, int coff)
+    {
+        Voxel v;
+        v.a = BrickFmt<8, ST>::load(p, coff);
+        v.b = BrickFmt<8, ST>::load(p + M.off, coff);
         return v;
     }
     __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
@@ -144,6 +168,9 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
 {
     constexpr int REC = Model::kStride;
     constexpr bool kZero = Model::kZeroNoop;
+    constexpr bool kSplit = SplitOf<Model>::value;
+    constexpr int XS = kSplit ? SplitOf<Model>::stride : REC;  // floats between x neighbours of a row
+    static_assert(!kSplit || Model::kEarlyLoad, "float32 brick rows are read at the top of the step");
     const float* __restrict__ batch_base = G.batch_base;
     const float ox = (float)i + 0.5f, oz = (float)j + 0.5f;
     const bool negx = dx < 0.0f, negz = dz < 0.0f;
@@ -161,7 +188,8 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
     int lx = (i - bx0 * DEX_BLOCK) >> mip, lz = (j - bz0 * DEX_BLOCK) >> mip;
     float Px = (float)(bx0 * DEX_BLOCK + (lx + (negx ? 0 : 1)) * vox - i) - 0.5f;
     float Pz = (float)(bz0 * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
-    const float* rp = batch_base + ((size_t)a0 * G.chain + level_offset(mip) + lz * side + lx) * REC;
+    // record (S) of the current voxel: rows of side voxels, x neighbours XS floats apart
+    const float* rp = batch_base + ((size_t)a0 * G.chain + level_offset(mip) + lz * side) * REC + lx * XS;
     float th_prev = 0.0f, tl_prev = 0.0f;
     // the step left the block: look up the next one and re-initialise the tracer
     // there (false: the ray ends)
@@ -208,7 +236,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
             Pz = (float)(bzc * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox - j) - 0.5f;
         }
         if (mip >= 0)
-            rp = batch_base + ((size_t)L.offset_of(key) * G.chain + level_offset(mip) + lz * side + lx) * REC;
+            rp = batch_base + ((size_t)L.offset_of(key) * G.chain + level_offset(mip) + lz * side) * REC + lx * XS;
         else if (kZero)
             rp = g_zero_record;
         return true;
@@ -222,7 +250,10 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
         // models with kEarlyLoad issue the current voxel's record before the
         // stepping and crossing bookkeeping, which then hides its latency
         if constexpr (Model::kEarlyLoad) {
-            if (kZero || mip >= 0) cur = model_load<Model>(M, rp);
+            if (kZero || mip >= 0) {
+                if constexpr (kSplit) cur = Model::load_split(M, rp, side * XS);
+                else cur = model_load<Model>(M, rp);
+            }
         }
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
@@ -237,7 +268,7 @@ __device__ __forceinline__ void trace_ray(const Geo& G, const typename Model::Pa
         if (on_x) {
             lx += sx;
             Px += negx ? -fvox : fvox;
-            rp += negx ? -REC : REC;
+            rp += negx ? -XS : XS;
             cross = (unsigned)lx >= (unsigned)side;
         } else {
             lz += sz;

@@ -31,13 +31,18 @@ __device__ __forceinline__ unsigned long long global_ns()
 template <int W>
 struct StaticRec {
     static constexpr int kStride = 2 * W;
+    static constexpr bool kSplit = true;  // float32 brick rows: S of the row, then chi
+    static constexpr int kSplitStride = W;
     static constexpr bool kEarlyLoad = true;  // as the float32 static model of the single-grid solve
     static constexpr bool kZeroNoop = true;
     struct Params {
         int unused;
     };
     using Voxel = Record<W>;
-    __device__ __forceinline__ static Voxel load(const float* p) { return RecFmt<W, kStoreF32>::load(p); }
+    __device__ __forceinline__ static Voxel load_split(const Params&, const float* p, int coff)
+    {
+        return BrickFmt<W, kStoreF32>::load(p, coff);
+    }
     __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
                                                      float* I, float* T)
     {

@@ -34,6 +34,8 @@ namespace {
 template <int W, int ST = kStoreF32>
 struct StaticModel {
     static constexpr int kStride = RecFmt<W, ST>::kStride;
+    static constexpr bool kSplit = BrickFmt<W, ST>::kSplit;  // float32: brick rows of S, then chi
+    static constexpr int kSplitStride = BrickFmt<W, ST>::kX;
     static constexpr bool kPerBatch = true;
     static constexpr int kMinBlocks = 4;  // CTAs per SM the register budget targets
     // record loaded at the top of each step: -3.3% (float32) on the 1024^2 benchmark
@@ -45,6 +47,10 @@ struct StaticModel {
     };
     using Voxel = Record<W>;
     __device__ __forceinline__ static Voxel load(const float* p) { return RecFmt<W, ST>::load(p); }
+    __device__ __forceinline__ static Voxel load_split(const Params&, const float* p, int coff)
+    {
+        return BrickFmt<W, ST>::load(p, coff);
+    }
     __device__ __forceinline__ static void integrate(const Params&, const Voxel& v, int, float, float, float nl2,
                                                      float* I, float* T)
     {

@@ -72,7 +72,8 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
                                              const int* __restrict__ s_info, float* I, float* T, unsigned int& nseg,
                                              bool& capped)
 {
-    constexpr int REC = RecFmt<8, ST>::kStride;
+    using BF = BrickFmt<8, ST>;
+    constexpr int REC = BF::kRec;
     const int cap = 2 * (G.nx + G.nz) + 64;
     const float ox = (float)i + 0.5f, oz = (float)j + 0.5f;
     const bool negx = dx < 0.0f, negz = dz < 0.0f;
@@ -107,7 +108,7 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
 #pragma unroll
         for (int q = 0; q < NB; ++q) {
             const int m = max(lev[q], 0), sh = max(m - mip, 0);
-            rp[q] = blk + slot_off[q] + (size_t)(level_offset(m) + (lz >> sh) * (DEX_BLOCK >> m) + (lx >> sh)) * REC;
+            rp[q] = blk + slot_off[q] + BF::offset(level_offset(m), lz >> sh, lx >> sh, DEX_BLOCK >> m);
             th0[q] = 0.0f;
             tl0[q] = 0.0f;
         }
@@ -119,7 +120,7 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
         // records of the voxels entered at the last plane, issued before the step's arithmetic
 #pragma unroll
         for (int q = 0; q < NB; ++q)
-            if ((fresh >> q) & 1u) rec[q] = RecFmt<8, ST>::load(rp[q]);
+            if ((fresh >> q) & 1u) rec[q] = BF::load(rp[q], BF::chi_off(DEX_BLOCK >> max(lev[q], 0)));
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
         const float th = on_x ? tnx : tnz;
@@ -162,7 +163,7 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
                 for (int q = 0; q < NB; ++q) {
                     if ((ends >> q) & 1u) {
                         const int row = DEX_BLOCK >> lev[q];
-                        rp[q] += on_x ? (negx ? -REC : REC) : (negz ? -row * REC : row * REC);
+                        rp[q] += on_x ? (negx ? -BF::kX : BF::kX) : (negz ? -row * REC : row * REC);
                         th0[q] = th;
                         tl0[q] = tl;
                     }
@@ -229,8 +230,7 @@ __device__ __forceinline__ void trace_ray_mb(const Geo& G, const long long* __re
 #pragma unroll
                 for (int q = 0; q < NB; ++q) {
                     const int m = max(lev[q], 0), sh = max(m - mip, 0);
-                    rp[q] = blk + slot_off[q] +
-                            (size_t)(level_offset(m) + (lz >> sh) * (DEX_BLOCK >> m) + (lx >> sh)) * REC;
+                    rp[q] = blk + slot_off[q] + BF::offset(level_offset(m), lz >> sh, lx >> sh, DEX_BLOCK >> m);
                 }
                 next_fresh = live;
             }

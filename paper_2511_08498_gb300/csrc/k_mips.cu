@@ -27,13 +27,17 @@ constexpr int kMaxLevels = 5;  // levels 0..4 of a 16 x 16 block
 
 __host__ __device__ constexpr int level_offset(int m) { return 341 - (341 >> (2 * m)); }
 
+// voxel (lx, lz) of the level of `side` voxels per row starting at voxel `first`
+// of the block's chain `brick` (BrickFmt: float32 rows hold S, then chi)
 template <int W, int ST>
-__device__ __forceinline__ void store_record(float* rec, const float* e, const float* c)
+__device__ __forceinline__ void store_record(float* brick, int first, int lz, int lx, int side, const float* e,
+                                             const float* c)
 {
+    using BF = BrickFmt<W, ST>;
     float S[W], x[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) encode_voxel(e[w], c[w], S[w], x[w]);
-    RecFmt<W, ST>::store(rec, S, x);
+    BF::store(brick + BF::offset(first, lz, lx, side), BF::chi_off(side), S, x);
 }
 
 template <int W, int ST>
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(256) k_mips_build(const MipParams P)
             sm_c[t][w] = cv;
         }
         if (bad) raise_status(P.status, DEX_ERR_NUMERIC);
-        store_record<W, ST>(brick + (size_t)t * REC, e, x_);
+        store_record<W, ST>(brick, 0, t >> 4, t & 15, DEX_BLOCK, e, x_);
     }
     __syncthreads();
 
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(256) k_mips_build(const MipParams P)
                 sm_e[off + t][w] = se.val;
                 sm_c[off + t][w] = sc.val;
             }
-            store_record<W, ST>(brick + (size_t)(off + t) * REC, e, x_);
+            store_record<W, ST>(brick, off, vz, vx, side, e, x_);
         }
         const int all = __syncthreads_and(pass ? 1 : 0);
         if (ok && all) level = m;

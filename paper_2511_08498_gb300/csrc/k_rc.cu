@@ -56,7 +56,8 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
                                             float dx, float dz, float* I, float* T, unsigned int& nseg,
                                             bool& capped)
 {
-    constexpr int REC = RecFmt<W, ST>::kStride;
+    using BF = BrickFmt<W, ST>;
+    constexpr int REC = BF::kRec;
     const bool negx = dx < 0.0f, negz = dz < 0.0f;
     const int sx = negx ? -1 : 1, sz = negz ? -1 : 1;
     const AxisParam ax = axis_param(dx), az = axis_param(dz);
@@ -80,7 +81,7 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
     float Pz = (float)(bzc * DEX_BLOCK + (lz + (negz ? 0 : 1)) * vox) - oz;
     const float* rp = base;
     if (mip >= 0)
-        rp = base + ((size_t)P.block_offset[blk] * P.chain + rc_level_offset(mip) + lz * side + lx) * REC;
+        rp = base + BF::offset((long long)P.block_offset[blk] * P.chain + rc_level_offset(mip), lz, lx, side);
     float th_prev = P.t_s, tl_prev = 0.0f;
 
     Record<W> r, r2;
@@ -88,8 +89,8 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
         // the current voxel's record is issued first: the stepping and crossing
         // bookkeeping below hides its latency
         if (mip >= 0) {
-            r = RecFmt<W, ST>::load(rp);
-            if constexpr (NB == 2) r2 = RecFmt<W, ST>::load(rp + off);
+            r = BF::load(rp, BF::chi_off(side));
+            if constexpr (NB == 2) r2 = BF::load(rp + off, BF::chi_off(side));
         }
         const float tnx = Px * ax.ih, tnz = Pz * az.ih;
         const bool on_x = tnx <= tnz;
@@ -109,7 +110,7 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
             if (on_x) {
                 lx += sx;
                 Px += negx ? -fv : fv;
-                rp += negx ? -REC : REC;
+                rp += negx ? -BF::kX : BF::kX;
                 cross = (unsigned)lx >= (unsigned)side;
             } else {
                 lz += sz;
@@ -156,7 +157,7 @@ __device__ __forceinline__ bool rc_interval(const RcParams& P, const float* __re
                 bxc = bxn;
                 bzc = bzn;
                 if (mip >= 0)
-                    rp = base + ((size_t)P.block_offset[blk] * P.chain + rc_level_offset(mip) + lz * side + lx) * REC;
+                    rp = base + BF::offset((long long)P.block_offset[blk] * P.chain + rc_level_offset(mip), lz, lx, side);
             }
         }
         if (cur_mip >= 0) {

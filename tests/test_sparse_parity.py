@@ -135,7 +135,9 @@ def test_vlm_levels_and_mip_values(ctx, max_mip, te, log_mean):
         for lvl in range(max_mip + 1):
             side = 16 >> lvl
             for b in range(L // W):
-                rec = bricks[b, r, off[lvl]:off[lvl] + side * side]  # [side*side][2W]
+                # float32 brick rows: the S values of the row's voxels, then their chi values
+                rows = bricks[b, r, off[lvl]:off[lvl] + side * side].reshape(side, 2, side, W)
+                rec = np.concatenate([rows[:, 0].reshape(-1, W), rows[:, 1].reshape(-1, W)], axis=1)  # [side*side][2W]
                 e_m = levels[lvl][0][b * W:(b + 1) * W, bz * side:(bz + 1) * side, bx * side:(bx + 1) * side]
                 c_m = levels[lvl][1][b * W:(b + 1) * W, bz * side:(bz + 1) * side, bx * side:(bx + 1) * side]
                 c_ref = c_m.reshape(W, -1).T
