@@ -660,6 +660,16 @@ int dex_batch_solve_noalloc(dex_ctx* ctx, int n_atm, const dex_batch_item* atms,
  * memory.  No paper counterpart (a measurement utility). */
 int dex_measure_ex2_rate(dex_ctx* ctx, double* ops_per_s);
 
+/* Measured throughput (lane operations per second) of the FP32 pipe on packed
+ * fused multiply-adds (FFMA2: two lane operations per instruction) on the
+ * context's device: the unit every multiply and add of the segment update
+ * (Eq. RteIntegral with the 1 - e^{-tau} series) occupies, and with ten of them
+ * per segment-wavelength the tighter of the solvers' two arithmetic ceilings.
+ * Runs a short probe kernel (8 x SMs CTAs, ~1 ms) on the context's stream and
+ * synchronises it; allocates and frees 1.2 MB of device memory.  No paper
+ * counterpart (a measurement utility). */
+int dex_measure_fp32_rate(dex_ctx* ctx, double* ops_per_s);
+
 /* Self-test of the device-side failure path: one thread waits on an mbarrier
  * that nothing arrives on, with the same bounded wait the tensor-core kernels
  * use, giving up after `polls` (1 .. 1e6) polls; the next dex_ctx_check then

@@ -75,6 +75,7 @@ PROTOTYPES = {
     "dex_batch_solve_config": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "dex_batch_solve_noalloc": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "dex_measure_ex2_rate": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "dex_measure_fp32_rate": (c_int, [c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "dex_selftest_wait_timeout": (c_int, [c_void_p, c_int]),
     "dex_mlp_param_count": (c_int, []),
     "dex_mlp_forward": (c_int, [c_void_p, ctypes.c_longlong, c_void_p, c_void_p, c_void_p]),

@@ -742,6 +742,14 @@ def measure_ex2_rate(ctx: Context) -> float:
     return float(v.value)
 
 
+def measure_fp32_rate(ctx: Context) -> float:
+    """Measured FP32-pipe throughput on packed fused multiply-adds (``dex_measure_fp32_rate``),
+    lane operations per second."""
+    v = ctypes.c_double(0.0)
+    ctx._rc(lib().dex_measure_fp32_rate(ctx.handle, ctypes.byref(v)))
+    return float(v.value)
+
+
 def selftest_wait_timeout(ctx: Context, polls: int = 1000):
     """Run the bounded-wait self-test (``dex_selftest_wait_timeout``); the next
     :meth:`Context.check` raises with DEX_ERR_TIMEOUT."""

@@ -1167,6 +1167,16 @@ int dex_measure_ex2_rate(dex_ctx* ctx, double* ops_per_s)
     return ok(ctx);
 }
 
+int dex_measure_fp32_rate(dex_ctx* ctx, double* ops_per_s)
+{
+    if (!ctx) return DEX_ERR_ARG;
+    if (!ops_per_s) return fail(ctx, DEX_ERR_ARG, "null output");
+    if (int r = bind(ctx)) return r;
+    cudaError_t e = dex::measure_fp32_rate(ctx->stream, ops_per_s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fp32 rate probe");
+    return ok(ctx);
+}
+
 int dex_selftest_wait_timeout(dex_ctx* ctx, int polls)
 {
     if (!ctx) return DEX_ERR_ARG;

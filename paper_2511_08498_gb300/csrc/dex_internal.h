@@ -259,6 +259,7 @@ int chain_length(int max_mip);
 int record_floats(int W, int storage);
 // special-function-unit 2^x throughput (k_probe.cu); synchronises the stream
 cudaError_t measure_ex2_rate(cudaStream_t s, double* ops_per_s);
+cudaError_t measure_fp32_rate(cudaStream_t s, double* ops_per_s);
 // a bounded mbarrier wait that runs out (self-test of the timeout path)
 cudaError_t launch_wait_timeout(cudaStream_t s, int polls, unsigned int* status);
 
