@@ -14,9 +14,10 @@
 // The block level is the largest m <= max_mip such that every group at every
 // level <= m passes for every wavelength of the batch, optionally capped per
 // block.  Every level of the chain is written as wavelength-batch records
-// (S, chi) in the requested storage format (float32, bfloat16, or float16 with
-// per-record scales); the level goes into the packed 3-bit state words
-// (0 = empty, m + 1 = level m, 21 blocks per 64-bit word).
+// (S, chi) in the requested storage format (float32, stored per brick row as
+// the row's S values then its chi values; bfloat16, or float16 with per-record
+// scales, one record per voxel: BrickFmt); the level goes into the packed 3-bit
+// state words (0 = empty, m + 1 = level m, 21 blocks per 64-bit word).
 #include "vlm.cuh"
 
 namespace dex {
