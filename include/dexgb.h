@@ -95,7 +95,7 @@ int dex_ctx_set_stream(dex_ctx* ctx, void* stream);
  *     that of the per-batch walk.  J and I equal, bit for bit, those of the
  *     per-batch walk given state words that hold the pair's minimum for both
  *     batches.  The middle batch of a group of odd size is solved by the
- *     per-batch walk.  Needs W = 8 and grids of at most 8192 blocks (the
+ *     per-batch walk.  Needs W = 8 and grids of at most 16384 blocks (the
  *     own-cell emission may be left out, dex_ctx_set_own_cell, as for the
  *     per-batch walk); otherwise dex_formal_solve_hdda returns
  *     DEX_ERR_UNSUPPORTED.  The executed segment

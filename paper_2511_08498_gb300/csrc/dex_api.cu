@@ -510,7 +510,7 @@ static int solve_sparse(dex_ctx* ctx, int kind, int nx, int nz, int n_lambda, in
     P.status = ctx->status;
     if (kind == 0 && P.traversal == DEX_TRAVERSAL_PAIRED && !dex::solve_hdda_paired_applies(P))
         return fail(ctx, DEX_ERR_UNSUPPORTED, "the paired walk needs W = 8 and at most %d blocks",
-                    dex::kInfoMaxBlocks);
+                    dex::kPairInfoMaxBlocks);
     if (int r = bind(ctx)) return r;
     cudaError_t e = cudaMemsetAsync(J, 0, sizeof(float) * (size_t)n_lambda * (size_t)P.n_cells, ctx->stream);
     if (e == cudaSuccess && I)

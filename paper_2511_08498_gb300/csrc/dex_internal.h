@@ -40,6 +40,10 @@ struct MipParams {
 
 // Grids of at most this many blocks stage the one-word-per-block table (32 KB).
 constexpr int kInfoMaxBlocks = 8192;
+// The paired walk always stages it, for grids of up to 2048 x 2048 (64 KB of
+// dynamic shared memory: with its 16 KB J tile, two 256-thread CTAs per SM
+// hold 160 KB).
+constexpr int kPairInfoMaxBlocks = 16384;
 
 // Distance thresholds of levels 1..4 padded to four, as the traversal compares
 // them (the number of thresholds band[m-1] <= t is the highest level allowed):

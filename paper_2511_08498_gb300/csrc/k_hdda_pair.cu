@@ -27,14 +27,19 @@ namespace dex {
 namespace {
 
 // Launch shape per brick format.  The pair's state (16 intensities and
-// transmissions, two records loaded at the top of each step) takes about 120
+// transmissions, two records loaded at the top of each step) takes about 125
 // registers with float32 records: 2 CTAs of 256 threads per SM.  Bfloat16
 // records hold half the registers and run at 5 CTAs of 128 threads (at most 102
 // registers).  Measured on the 1024^2 static-line solve (IoD 1e-2 / unlimited
-// averaging):
-//   float32, 256 threads, 2 CTAs (this)         173.6 / 62.8 ms
+// averaging), float32 on brick rows:
+//   float32, 256 threads, 2 CTAs (this)          158.8 / 63.3 ms
+//   float32, 128 threads, 4 CTAs                 167.1 / 66.8 ms
+//   float32, 128 threads, 3 CTAs (160 registers) 168.0 / 67.5 ms
+//   float32, 64 threads, 8 CTAs                  167.6 / 67.4 ms
+//   float32, 256 threads, 1 CTA (194 registers)  204.5 / 82.0 ms
+// with float32 records of S and chi side by side (before the brick rows):
+//   float32, 256 threads, 2 CTAs                 173.6 / 62.8 ms
 //   float32, 128 threads, 5 CTAs (96 registers)  176.4 / 66.1 ms
-//   float32, 128 threads, 4 CTAs                 173.8 / 66.0 ms
 //   float32, 256 threads, 3 CTAs (80, spills)    294.4 / 106.1 ms
 //   bfloat16, 128 threads, 5 CTAs (this)         165.0 / 66.2 ms
 //   bfloat16, 256 threads, 2 CTAs                171.5 / 66.6 ms
@@ -183,7 +188,7 @@ cudaError_t launch_pair(cudaStream_t s, const HddaParams& P)
 bool solve_hdda_paired_applies(const HddaParams& P)
 {
     const long long n_blocks = (long long)P.nbx * P.nbz;
-    return P.traversal == DEX_TRAVERSAL_PAIRED && P.W == 8 && n_blocks <= kInfoMaxBlocks &&
+    return P.traversal == DEX_TRAVERSAL_PAIRED && P.W == 8 && n_blocks <= kPairInfoMaxBlocks &&
            (!P.exclude_own || P.storage == kStoreF32);
 }
 

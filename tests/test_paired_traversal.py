@@ -257,3 +257,59 @@ def test_paired_walk_without_own_cell(ctx):
         ctx.set_own_cell(True)
     assert np.array_equal(Ic, Ip)
     assert np.array_equal(Jc, Jp)
+
+
+def _banded_grid(nx, nz, L, rows):
+    """eta, chi on device: a smooth medium in the bottom `rows` cells, the same at
+    every wavelength (so every batch takes the same levels), empty above."""
+    x = torch.arange(nx, device="cuda", dtype=torch.float32)[None, :] + 0.5
+    z = torch.arange(rows, device="cuda", dtype=torch.float32)[:, None] + 0.5
+    chi_b = 0.05 * (1.5 + torch.sin(2 * np.pi * x / 300.0)) * torch.exp(-z / 20.0)
+    eta_b = chi_b * (1.0 + 0.5 * torch.cos(2 * np.pi * x / 170.0))
+    chi = torch.zeros((L, nz, nx), device="cuda")
+    eta = torch.zeros_like(chi)
+    chi[:, :rows, :] = chi_b
+    eta[:, :rows, :] = eta_b
+    return eta.reshape(L, -1), chi.reshape(L, -1)
+
+
+def test_paired_walk_above_the_per_batch_staged_table(ctx):
+    """The paired walk stages one word per block for grids of up to 16384 blocks (the
+    per-batch walk only up to 8192, reading the packed words beyond): on a 2560 x 1024
+    grid (10240 blocks) the paired walk equals the per-batch walk bit for bit."""
+    from paper_2511_08498_gb300 import api
+    nx, nz, L = 2560, 1024, 16
+    eg, cg = _banded_grid(nx, nz, L, 64)
+    grid = api.grid_build(ctx, nx, nz, eg, cg)
+    assert 8192 < grid.n_blocks <= 16384
+    mp = api.mips_build(ctx, grid, eg, cg, W, 3, 1e-2, 1e-2, 0.25, log_mean=False, capacity=grid.n_active())
+    dirs, w = synth.directions(8)
+    band = [6.0, 24.0, 96.0]
+    Jb, _, _ = api.formal_solve_hdda(ctx, grid, mp, dirs, w, band=band)
+    ctx.set_traversal(api.TRAVERSAL_PAIRED)
+    try:
+        Jp, _, _ = api.formal_solve_hdda(ctx, grid, mp, dirs, w, band=band)
+    finally:
+        ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+    ctx.check()
+    assert float(Jb.abs().max()) > 0.0
+    assert torch.equal(Jb, Jp)
+
+
+def test_paired_walk_refuses_grids_above_16384_blocks(ctx):
+    from paper_2511_08498_gb300 import api
+    nx, nz, L = 4096, 1040, 8
+    eg, cg = _banded_grid(nx, nz, L, 16)
+    grid = api.grid_build(ctx, nx, nz, eg, cg)
+    assert grid.n_blocks > 16384
+    mp = api.mips_build(ctx, grid, eg, cg, W, 3, 1e-2, 1e-2, 0.25, log_mean=False, capacity=grid.n_active())
+    dirs, w = synth.directions(4)
+    ctx.set_traversal(api.TRAVERSAL_PAIRED)
+    try:
+        with pytest.raises(api.DexError) as ex:
+            api.formal_solve_hdda(ctx, grid, mp, dirs, w)
+        assert ex.value.code == 16   # DEX_ERR_UNSUPPORTED
+    finally:
+        ctx.set_traversal(api.TRAVERSAL_PER_BATCH)
+    J, _, _ = api.formal_solve_hdda(ctx, grid, mp, dirs, w)   # the per-batch walk takes it
+    ctx.check()
