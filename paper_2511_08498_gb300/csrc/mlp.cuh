@@ -21,15 +21,37 @@ struct Act {
     float g, dg;
 };
 
-// GELU, tanh form: g(z) = z/2 (1 + tanh(c (z + k z^3))), c = sqrt(2/pi), k = 0.044715
+// GELU, tanh form: g(z) = z/2 (1 + tanh(u)), u = c (z + k z^3), c = sqrt(2/pi),
+// k = 0.044715.  Evaluated through the identity 1/2 (1 + tanh u) = 1 / (1 + e^{-2u})
+// (the logistic function of 2u): s = 1 / (1 + 2^{-2u log2 e}) with the
+// special-function unit's 2^x and reciprocal, g = z s.  Nothing cancels, so s and
+// g carry a few float32 ulps of relative error for every z (a large -2u makes
+// 2^x overflow to +inf and s = 0, g = 0; a large u makes 2^x flush to 0 and s = 1).
+//   g' = s + z s (1 - s) 2 u',  u' = c (1 + 3 k z^2).
+__device__ __forceinline__ float mlp_ex2(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float mlp_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ Act gelu(float z)
 {
     const float c = 0.79788456080286536f, k = 0.044715f;
+    const float m2log2e = -2.8853900817779268f;  // -2 log2(e)
     const float z2 = z * z;
-    const float t = tanhf(c * fmaf(k * z2, z, z));
+    const float u = c * z * fmaf(k, z2, 1.0f);
+    const float s = mlp_rcp(1.0f + mlp_ex2(u * m2log2e));
     Act r;
-    r.g = 0.5f * z * (1.0f + t);
-    r.dg = fmaf(0.5f * z * (1.0f - t * t) * c, fmaf(3.0f * k, z2, 1.0f), 0.5f * (1.0f + t));
+    r.g = z * s;
+    r.dg = fmaf(z * s * (1.0f - s), 2.0f * c * fmaf(3.0f * k, z2, 1.0f), s);
     return r;
 }
 
