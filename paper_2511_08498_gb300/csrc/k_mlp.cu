@@ -24,6 +24,7 @@
 // records DEX_ERR_TIMEOUT, waits (bounded) once more, frees its tensor memory
 // and returns.
 #include <cmath>
+#include <cstddef>
 
 #include "dex_internal.h"
 #include "mlp.cuh"
@@ -60,6 +61,7 @@ struct SmemInfer {
     unsigned char W2[kH * kH * 2];        // B of D2: rows out j, K in i
     unsigned char H1[kTile * kH * 2];     // A of D2: rows sample, K in i
     float w1[kH * 3], b1[kH], b2[kH], w3[kH], b3;
+    alignas(16) float w1t[3][kH];         // w1 by input feature: neighbouring units side by side
     unsigned long long mbar;
     unsigned int tmem;
 };
@@ -83,6 +85,10 @@ struct SmemTrain {
 constexpr size_t kSmemInfer = 48 * 1024;
 constexpr size_t kSmemTrain = 110 * 1024;
 static_assert(sizeof(SmemInfer) <= kSmemInfer, "inference shared memory");
+// the packed inference loads read float2 pairs of these arrays at even indices
+static_assert(offsetof(SmemInfer, b1) % 8 == 0 && offsetof(SmemInfer, b2) % 8 == 0 &&
+                  offsetof(SmemInfer, w3) % 8 == 0 && offsetof(SmemInfer, w1t) % 8 == 0,
+              "inference weight alignment");
 static_assert(sizeof(SmemTrain) <= kSmemTrain, "training shared memory");
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -143,6 +149,41 @@ __device__ __forceinline__ void layer1(S& sm, const float* f, int t, unsigned ch
     }
 }
 
+// GELU of two hidden units at once on the packed FP32 pipe (FMUL2/FFMA2/FADD2):
+// every lane rounded exactly as mlp::gelu(z).g
+__device__ __forceinline__ float2 gelu2(float2 z)
+{
+    const float c = 0.79788456080286536f, k = 0.044715f;
+    const float m2log2e = -2.8853900817779268f;
+    const float2 z2 = __fmul2_rn(z, z);
+    const float2 u = __fmul2_rn(__fmul2_rn(make_float2(c, c), z), __ffma2_rn(make_float2(k, k), z2, make_float2(1.0f, 1.0f)));
+    const float2 a = __fmul2_rn(u, make_float2(m2log2e, m2log2e));
+    const float2 d = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(mlp::mlp_ex2(a.x), mlp::mlp_ex2(a.y)));
+    return __fmul2_rn(z, make_float2(mlp::mlp_rcp(d.x), mlp::mlp_rcp(d.y)));
+}
+
+// layer 1 + GELU for sample row t (inference): units in pairs on the packed pipe,
+// every value rounded as in layer1()
+__device__ __forceinline__ void layer1_infer(SmemInfer& sm, const float* f, int t)
+{
+    const float2 f0 = make_float2(f[0], f[0]), f1 = make_float2(f[1], f[1]), f2 = make_float2(f[2], f[2]);
+#pragma unroll 1
+    for (int i0 = 0; i0 < kH; i0 += 8) {
+        __align__(16) __nv_bfloat162 hb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + 2 * q;
+            const float2 b = *reinterpret_cast<const float2*>(&sm.b1[i]);
+            const float2 w0 = *reinterpret_cast<const float2*>(&sm.w1t[0][i]);
+            const float2 w1 = *reinterpret_cast<const float2*>(&sm.w1t[1][i]);
+            const float2 w2 = *reinterpret_cast<const float2*>(&sm.w1t[2][i]);
+            const float2 z = __ffma2_rn(w2, f2, __ffma2_rn(w1, f1, __ffma2_rn(w0, f0, b)));
+            hb[q] = __float22bfloat162_rn(gelu2(z));
+        }
+        *reinterpret_cast<uint4*>(sm.H1 + tile_offset(t, i0, kTile)) = *reinterpret_cast<const uint4*>(hb);
+    }
+}
+
 // one MMA chain: D (+)= A B^T over K/16 K-steps, issued by the calling thread
 __device__ __forceinline__ void mma_chain(uint32_t d, const unsigned char* A, int rowsA, const unsigned char* B,
                                           int rowsB, int K, uint32_t idesc, bool accumulate)
@@ -180,6 +221,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward(const MlpParams P)
     SmemInfer& sm = *reinterpret_cast<SmemInfer*>(smem_raw);
     const int t = threadIdx.x, warp = t >> 5;
     stage_weights(sm, P.params, false, nullptr);
+    for (int q = t; q < kH * 3; q += blockDim.x) sm.w1t[q % 3][q / 3] = bf16_round(P.params[kW1 + q]);
     if (t == 0) mbar_init(&sm.mbar, 1);
     if (warp == 0) tmem_alloc(&sm.tmem, kColsInfer);
     sync_for_mma();
@@ -195,21 +237,27 @@ __global__ void __launch_bounds__(128, 1) k_mlp_forward(const MlpParams P)
             raise_status(P.status, DEX_ERR_NUMERIC);
             valid = false;
         }
-        layer1(sm, f, t, nullptr);
+        layer1_infer(sm, f, t);
         sync_for_mma();
         if (t == 0) {
             mma_chain(tm + kColD2, sm.H1, kTile, sm.W2, kH, kH, idesc_bf16_f32(kTile, kH), false);
             mma_commit(&sm.mbar);
         }
         if (!(ok = wait_all(&sm.mbar, phase))) break;
-        float y = sm.b3;
+        // output unit: two partial sums (even and odd hidden units) on the packed pipe
+        float2 y2 = make_float2(sm.b3, 0.0f);
 #pragma unroll 1
         for (int c = 0; c < kH; c += 16) {
             float z[16];
             tmem_ld16(tmem_at(tm, warp * 32, kColD2 + c), z);
 #pragma unroll
-            for (int q = 0; q < 16; ++q) y = fmaf(sm.w3[c + q], gelu(z[q] + sm.b2[c + q]).g, y);
+            for (int q = 0; q < 16; q += 2) {
+                const float2 b = *reinterpret_cast<const float2*>(&sm.b2[c + q]);
+                const float2 w = *reinterpret_cast<const float2*>(&sm.w3[c + q]);
+                y2 = __ffma2_rn(w, gelu2(__fadd2_rn(make_float2(z[q], z[q + 1]), b)), y2);
+            }
         }
+        const float y = y2.x + y2.y;
         if (valid) P.out[s] = y;
     }
     if (!ok) {
