@@ -14,7 +14,12 @@ computing those probes one by one:
   are that close: each may take either of two levels (float32 and float64
   decide them differently), so the oracle solves every combination of those
   candidate levels and J must match one of them at 1e-5 -- always, whichever
-  way the GPU decided (its levels there must be among the candidates).
+  way the GPU decided (its levels there must be among the candidates);
+* the walk the benchmark times, one walk per mirror pair of wavelength batches
+  (DEX_TRAVERSAL_PAIRED): with unlimited averaging against the oracle's banded
+  solve on the pair-minimum level map at 1e-5, and at IoD 1e-2 equal bit for
+  bit to the one-walk-per-batch solve checked above, the mirrored batches'
+  levels agreeing in every block of this atmosphere.
 """
 
 import itertools
@@ -68,14 +73,23 @@ def test_plain_full_size_sampled(case):
     assert rel(Jg, Jr).max() < 1e-5
 
 
-def _accelerated(c, iod):
+def _accelerated(c, iod, paired=False, full=False):
     api = c["api"]
     grid = api.grid_build(c["ctx"], N, N, c["eg"], c["cg"])
     mips = api.mips_build(c["ctx"], grid, c["eg"], c["cg"], W, MAX_MIP, iod, iod, 0.25, log_mean=False)
-    J, _, _ = api.formal_solve_hdda(c["ctx"], grid, mips, c["dirs"], c["w"], band=BAND)
-    c["ctx"].check()
+    c["ctx"].set_traversal(api.TRAVERSAL_PAIRED if paired else api.TRAVERSAL_PER_BATCH)
+    try:
+        J, _, _ = api.formal_solve_hdda(c["ctx"], grid, mips, c["dirs"], c["w"], band=BAND)
+        c["ctx"].check()
+    finally:
+        c["ctx"].set_traversal(api.TRAVERSAL_PER_BATCH)
     glev = api.unpack_states(mips.words.cpu().numpy(), grid.n_blocks).reshape(-1, N // 16, N // 16)
-    return J.cpu().numpy()[:, c["sample"]], glev
+    return (J if full else J.cpu().numpy()[:, c["sample"]]), glev
+
+
+def _pair_min(lev):
+    """Per batch, the smaller of its own level and its mirror batch's (-1 where empty)."""
+    return np.minimum(lev, lev[::-1])
 
 
 def test_accelerated_unlimited_full_size_sampled(case):
@@ -107,3 +121,21 @@ def test_accelerated_benchmark_threshold_full_size(case):
         Jr = lc.formal_solve_banded(levels, lv, 16, W, BAND, c["dirs"], c["w"], c["sample"])
         errs.append(float(rel(Jg, Jr).max()))
     assert min(errs) < 1e-5, errs
+
+
+def test_paired_walk_unlimited_full_size_sampled(case):
+    c = case
+    Jg, glev = _accelerated(c, 1e30, paired=True)
+    levels, passes = omips.mip_chain(c["er"], c["cr"], MAX_MIP, 1e30, 1e30, 0.25, mean="linear")
+    lev = omips.block_levels(passes, c["empty"], 16, W)
+    assert np.array_equal(glev, lev)
+    Jr = lc.formal_solve_banded(levels, _pair_min(lev), 16, W, BAND, c["dirs"], c["w"], c["sample"])
+    assert rel(Jg, Jr).max() < 1e-5
+
+
+def test_paired_walk_benchmark_threshold_equals_per_batch_walk(case):
+    c = case
+    Jp, glev = _accelerated(c, 1e-2, paired=True, full=True)
+    assert np.array_equal(_pair_min(glev), glev), "the mirrored batches' levels differ on this atmosphere"
+    Jb, _ = _accelerated(c, 1e-2, full=True)
+    assert torch.equal(Jp, Jb)
